@@ -1,0 +1,456 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 LBM-RANS step (MLUPS and HBM roofline).
+
+Workload (N = 1): the 3-D D3Q19 turbulent channel in FP32 storage,
+256 x 128 x 128 cells, periodic in x and z, slip-velocity bounce-back walls
+(Eq. 35) on both y faces, Re_tau = 5200, SA turbulence model, initial
+u_x = U_b (1 +/- 1 %) seeded.  A step is one full pass of the method: the
+wall pre-pass kernel and the fused SA + stream + collide kernel.  The
+population buffers (2 x 319 MB) are larger than the 129 MB L2, so no flush is
+needed between steps.
+
+Extra keys report the HRFD wall scheme, FP16/BF16 shifted storage and the
+batched mesh-sensitivity sweep on the same GPU.  ``--impl reference`` times the
+FP64 CPU oracle on a bounded crop of the same workload.
+
+Multi-GPU: one process per GPU (torchrun); every rank advances its own
+replica of the workload (weak scaling, no data-path collective); the timed
+region is bracketed by a barrier and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lbm_cases as C  # noqa: E402
+
+METRIC = "MLUPS and % of HBM roofline: FP32 vs FP16-storage vs batched, at C_f err ≤1%"
+WORKLOAD = dict(re_tau=5200.0, scheme="wall_bb", nx=256, ny=128, nz=128, seed=0)
+# algorithmic bytes per cell per step: read + write every population once,
+# read + write nu_tilde once (velocity and nu_t are recomputable, the wall
+# distance is analytic)
+ALG_BYTES = {("D3Q19", "fp32"): 160, ("D3Q19", "fp16"): 84, ("D3Q19", "bf16"): 84,
+             ("D3Q19", "fp64"): 320, ("D2Q9", "fp32"): 80, ("D2Q9", "fp16"): 44,
+             ("D2Q9", "bf16"): 44, ("D2Q9", "fp64"): 160}
+KERNEL_SOURCES = ["paper_2506_03905_gb300/csrc/lbm_kernels.cuh",
+                  "paper_2506_03905_gb300/csrc/lbm_device.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(case_key: str):
+    """dram bytes per launch of the bulk kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_bulk_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    entry = d.get(case_key)
+    if not entry or entry.get("kernel_hash") != kernel_hash():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_case(pkg, case, steps, warmup, torch):
+    """Device-resident timing (CUDA events on the solver's stream) and the
+    per-kernel durations of the same number of steps."""
+    s = pkg.Solver(case)
+    s.set_fields(*C.initial_fields(case))
+    s.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    bulk_ms, wall_ms = s.step_timed(steps)
+    d = s.diagnostics()
+    s.close()
+    return ms, bulk_ms / steps, wall_ms / steps, d
+
+
+def run_ours(args):
+    import torch
+    import paper_2506_03905_gb300 as pkg
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    pkg.lib()
+    case = C.channel_3d(**WORKLOAD, storage="fp32")
+    peak, peak_kind = measured_peaks()
+
+    # ---- headline: device-resident FP32 bounce-back channel
+    s = pkg.Solver(case)
+    s.set_fields(*C.initial_fields(case))
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(args.steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    # per-kernel durations over the same number of steps (events around each launch)
+    bulk_ms, wall_ms = s.step_timed(args.steps)
+    diag = s.diagnostics()
+    s.close()
+    cells = case.cells
+    value = cells * args.steps * world / (ms * 1e-3) / 1e6
+    bulk_avg = bulk_ms / args.steps
+    alg = ALG_BYTES[(case.lattice, case.storage)] * cells
+    achieved = alg / (bulk_avg * 1e-3) / 1e9
+    traffic = ncu_traffic("channel_3d_Re5200_wall_bb_256x128x128_fp32")
+
+    # ---- end to end through the C ABI with pinned host buffers
+    rho, u, nut = C.initial_fields(case)
+    pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+    h_rho, h_u, h_nut = pin(rho), pin(u), pin(nut)
+    h_out_u = torch.empty(u.shape, dtype=torch.float64).pin_memory()
+    h_out_nut = torch.empty(nut.shape, dtype=torch.float64).pin_memory()
+    s = pkg.Solver(case)
+    s.set_fields(rho, u, nut)
+    s.step(2)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    pkg.lbm_set_fields(s.ctx, h_rho.data_ptr(), h_u.data_ptr(), h_nut.data_ptr(), False)
+    s.step(args.steps)
+    st = pkg.lbm_fields(s.ctx, pkg.FIELD["u"] | pkg.FIELD["nu_t"],
+                       [h_out_u.data_ptr(), h_out_nut.data_ptr()], False)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    s.close()
+    h2d = (rho.nbytes + u.nbytes + nut.nbytes) / args.steps
+    d2h = (u.nbytes + nut.nbytes) / args.steps
+    e2e = cells * args.steps * world / e2e_s / 1e6
+
+    # ---- variants on the same GPU (rank 0 only, short)
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        vsteps = max(10, min(args.steps, 100))
+        for label, kw in [("fp32_hrfd", dict(scheme="wall_hrfd", storage="fp32")),
+                          ("fp16_bb", dict(storage="fp16")), ("bf16_bb", dict(storage="bf16")),
+                          ("fp16_hrfd", dict(scheme="wall_hrfd", storage="fp16"))]:
+            wk = dict(WORKLOAD)
+            wk.update({k: v for k, v in kw.items() if k != "storage"})
+            vc = C.channel_3d(**wk, storage=kw["storage"])
+            vms, vbulk, vwall, vd = time_case(pkg, vc, vsteps, 3, torch)
+            vb = ALG_BYTES[(vc.lattice, vc.storage)] * vc.cells
+            variants[label] = {
+                "mlups": round(vc.cells * vsteps / (vms * 1e-3) / 1e6, 1),
+                "bulk_ms": round(vbulk, 4), "wall_ms": round(vwall, 4),
+                "alg_bytes_per_cell": ALG_BYTES[(vc.lattice, vc.storage)],
+                "bulk_frac_of_hbm": round(vb / (vbulk * 1e-3) / 1e9 / peak, 4),
+                "nonfinite": int(vd.nonfinite)}
+        try:
+            variants.update(batched_variant(pkg, torch, vsteps))
+        except Exception as exc:  # the batched path reports its own status
+            variants["batched"] = {"unavailable": str(exc)[:200]}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "channel_3d_D3Q19_256x128x128_fp32_Re5200_slip_bounce_back",
+                   "lattice": "D3Q19", "nx": 256, "ny": 128, "nz": 128, "storage": "fp32",
+                   "collision": "bgk", "walls": "slip-velocity bounce-back (Eq. 35) both y faces",
+                   "turbulence": "Spalart-Allmaras", "cells": cells,
+                   "l2": "inputs larger than L2 (2 x 319 MB population buffers)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_bulk<19, fp32>",
+                     "alg_bytes_per_cell": ALG_BYTES[(case.lattice, case.storage)],
+                     "bulk_ms": round(bulk_avg, 4), "wall_pass_ms": round(wall_ms / args.steps, 4)},
+        "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "status": int(st)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "diagnostics": {"mass": diag.mass, "nonfinite": int(diag.nonfinite),
+                        "mean_u_tau": list(diag.mean_u_tau)},
+        "variants": variants,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def batched_variant(pkg, torch, steps):
+    cases = C.batched_sweep(96, storage="fp32")
+    solvers = []
+    for c in cases:
+        s = pkg.Solver(c)
+        s.set_fields(*C.initial_fields(c))
+        solvers.append(s)
+    total = sum(c.cells for c in cases)
+    out = {}
+    # per-case sequential runs (each graph-replayed)
+    for s in solvers:
+        s.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in solvers:
+        s.step(steps)
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t0
+    out["per_case_fp32"] = {"mlups": round(total * steps / seq / 1e6, 1), "instances": len(cases),
+                            "cells": total}
+    b = pkg.lbm_batch_create([s.ctx for s in solvers])
+    try:
+        pkg.lbm_batch_step(b, 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pkg.lbm_batch_step(b, steps)
+        torch.cuda.synchronize()
+        bt = time.perf_counter() - t0
+        out["batched_fp32"] = {"mlups": round(total * steps / bt / 1e6, 1), "instances": len(cases),
+                               "cells": total}
+    finally:
+        pkg.lbm_batch_destroy(b)
+        for s in solvers:
+            s.close()
+    return out
+
+
+def cpu_sample_case(nx: int = 64):
+    """Bounded sample of the workload for the CPU oracle: the same channel
+    physics on an nx x 128 x 8 crop (full wall-to-wall height)."""
+    wk = dict(WORKLOAD)
+    wk.update(nx=nx, nz=8)
+    return C.channel_3d(**wk, storage="fp64")
+
+
+_CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import lbm_cases as C
+from oracle import Oracle
+import bench
+case = bench.cpu_sample_case()
+o = Oracle(case, *C.initial_fields(case))
+o.step()
+n, t0 = 0, time.perf_counter()
+while time.perf_counter() - t0 < {seconds}:
+    o.step(); n += 1
+dt = time.perf_counter() - t0
+print(json.dumps(dict(steps=n, seconds=dt, cells=case.cells)))
+"""
+
+
+def cpu_baseline(seconds: float):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = _CPU_SNIPPET.format(root=ROOT, seconds=seconds)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": round(d["cells"] * d["steps"] / d["seconds"] / 1e6, 4), "unit": "MLUPS",
+            "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, same channel physics on a 64x128x8 crop, "
+                      f"{d['steps']} steps in {d['seconds']:.1f} s (one thread)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # crop sized so that the whole run stays within a few minutes
+    nx = max(4, min(64, int(64 * 200 / max(args.steps, 1)) // 4 * 4))
+    case = cpu_sample_case(nx)
+    from oracle import Oracle
+    o = Oracle(case, *C.initial_fields(case))
+    for _ in range(max(args.warmup, 0)):
+        o.step()
+    per_step = max(1, int(args.ref_steps_per_step))
+    t0 = time.perf_counter()
+    for _ in range(args.steps * per_step):
+        o.step()
+    dt = time.perf_counter() - t0
+    value = case.cells * args.steps * per_step / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "channel_3d_D3Q19_256x128x128_fp32_Re5200_slip_bounce_back",
+                       "sample": f"{nx}x128x8 crop of the workload, FP64 oracle"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"{nx}x128x8 crop, {per_step} oracle step(s) per timed step"},
+            "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_profile_case(args):
+    """Short run of one channel case for profilers: set-up, --warmup steps, then
+    --steps steps, each launched individually (no graph)."""
+    import torch
+    import paper_2506_03905_gb300 as pkg
+    case = C.channel_3d(re_tau=5200.0, scheme=args.scheme, nx=args.nx, ny=args.ny, nz=args.nz,
+                        storage=args.storage)
+    s = pkg.Solver(case)
+    s.set_fields(*C.initial_fields(case))
+    s.step_timed(args.warmup)
+    bulk, wall = s.step_timed(args.steps)
+    torch.cuda.synchronize()
+    s.close()
+    print(json.dumps({"profile_case": case.name, "storage": args.storage, "steps": args.steps,
+                      "bulk_ms": bulk / args.steps, "wall_ms": wall / args.steps}))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-steps-per-step", type=int, default=1)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="short per-launch run of one channel case (for ncu)")
+    ap.add_argument("--nx", type=int, default=256)
+    ap.add_argument("--ny", type=int, default=128)
+    ap.add_argument("--nz", type=int, default=64)
+    ap.add_argument("--scheme", default="wall_bb")
+    ap.add_argument("--storage", default="fp32")
+    args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

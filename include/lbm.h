@@ -1,0 +1,204 @@
+/*
+ * lbm.h -- C ABI of the GB300 LBM-RANS wall-function solver.
+ *
+ * The library advances the lattice Boltzmann equation (Section 2.1, Eqs. 1-8)
+ * on a uniform D2Q9 or D3Q19 lattice with the local relaxation time set by
+ * molecular plus Spalart-Allmaras eddy viscosity (Section 2.2, Eqs. 10-14),
+ * and imposes turbulent walls with either of the paper's two schemes:
+ *   - slip-velocity half-way bounce-back (Section 3.2, Eqs. 31-35), and
+ *   - the hybrid regularized condition with the blended wall-normal gradient
+ *     (HRFD, Section 3.1, Eqs. 17-28),
+ * both closed by the SA-consistent wall function (Eqs. 15-16) or the log law,
+ * inverted for u_tau by an FP64 Newton iteration.
+ *
+ * Conventions
+ *   - Every function returns an lbm_status; nothing throws across the ABI.
+ *   - All physical inputs and outputs are SI; the library converts to lattice
+ *     units with the acoustic scaling dt = M dx / (sqrt(3) U_ref) (Section 4.1.1).
+ *   - Field arrays are float64, x fastest: index (z*ny + y)*nx + x; vector
+ *     fields are component-major: comp*(nz*ny*nx) + cell.
+ *   - Wall-node arrays of a y face hold one value per (z, x) node of the face,
+ *     index z*nx + x, zero where the face is not a wall (x < x_start).
+ *   - The library owns every device buffer it allocates (through cfg.alloc if
+ *     given, else cudaMalloc) and never frees caller memory.
+ *   - Work is enqueued on cfg.stream; lbm_step returns as soon as the work is
+ *     enqueued. Functions that copy results to the caller synchronise that
+ *     stream and report device-side failure flags.
+ *   - Not thread-safe per context; distinct contexts are independent.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,        /* invalid argument or configuration */
+  LBM_ENOMEM = 2,        /* device or host allocation failed */
+  LBM_ECUDA = 3,         /* a CUDA runtime call failed (see lbm_last_error) */
+  LBM_ENONFINITE = 4,    /* a population, velocity or nu_tilde became NaN/Inf */
+  LBM_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+  LBM_ENEWTON = 6,       /* the u_tau inversion did not converge at some node */
+  LBM_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} lbm_status;
+
+enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 };
+enum { LBM_BGK = 0, LBM_REGULARIZED = 1 };
+enum { LBM_FP32 = 0, LBM_FP16_SHIFTED = 1, LBM_BF16_SHIFTED = 2, LBM_FP64 = 3 };
+enum { LBM_SA = 0, LBM_LAMINAR = 1 };
+enum { LBM_LAW_SA_ANALYTIC = 0, LBM_LAW_LOG = 1 };
+
+/* boundary kinds (lbm_bc.kind) */
+enum {
+  LBM_BC_PERIODIC = 0,
+  LBM_BC_WALL_SLIP_BB = 1,     /* Section 3.2: Eq. 31 with the slip velocity of Eq. 35 */
+  LBM_BC_WALL_HRFD = 2,        /* Section 3.1: Eq. 19 with Eqs. 23, 26-28 */
+  LBM_BC_SYMMETRY = 3,         /* specular reflection (free slip) */
+  LBM_BC_INLET_ZOUHE = 4,      /* Zou-He velocity inlet (xmin only) */
+  LBM_BC_OUTLET_ZEROGRAD = 5,  /* zero-gradient outlet (xmax only) */
+  LBM_BC_FREESTREAM = 6        /* incoming populations at f^eq(rho0, u_in) */
+};
+
+/* faces (lbm_set_bc face argument) */
+enum { LBM_XMIN = 0, LBM_XMAX = 1, LBM_YMIN = 2, LBM_YMAX = 3, LBM_ZMIN = 4, LBM_ZMAX = 5 };
+
+/* lbm_fields masks; dst[k] receives the k-th set bit in this order */
+enum {
+  LBM_FIELD_RHO = 1u << 0,      /* nz*ny*nx, kg/m^3 */
+  LBM_FIELD_U = 1u << 1,        /* 3*nz*ny*nx, m/s */
+  LBM_FIELD_NU_T = 1u << 2,     /* nz*ny*nx, m^2/s, nu_tilde * f_v1 (Eq. 10) */
+  LBM_FIELD_NU_TILDE = 1u << 3, /* nz*ny*nx, m^2/s */
+  LBM_FIELD_UTAU_YMIN = 1u << 4,/* nz*nx, m/s */
+  LBM_FIELD_UTAU_YMAX = 1u << 5,/* nz*nx, m/s */
+  LBM_FIELD_CF_YMIN = 1u << 6,  /* nz*nx, 2 (u_tau / U_ref)^2 */
+  LBM_FIELD_CF_YMAX = 1u << 7
+};
+
+typedef struct {
+  int lattice;                 /* LBM_D2Q9 | LBM_D3Q19 */
+  int nx, ny, nz;              /* cells; nz = 1 for D2Q9 */
+  double dx;                   /* m */
+  double nu;                   /* m^2/s */
+  double rho0;                 /* kg/m^3 */
+  double u_ref;                /* m/s, sets dt with mach */
+  double mach;                 /* dt = mach*dx/(sqrt(3)*u_ref) */
+  double force[3];             /* body acceleration g (m/s^2); F = rho0 g */
+  double origin[3];            /* physical coordinates of the domain's low corner */
+  int collision;               /* LBM_BGK | LBM_REGULARIZED */
+  int storage;                 /* LBM_FP32 | LBM_FP16_SHIFTED | LBM_BF16_SHIFTED | LBM_FP64 */
+  int turbulence;              /* LBM_SA | LBM_LAMINAR */
+  int wall_law;                /* LBM_LAW_SA_ANALYTIC (Eq. 16) | LBM_LAW_LOG */
+  double kappa, B;             /* log-law constants */
+  void* (*alloc)(size_t bytes, void* user);  /* optional device allocator */
+  void (*free)(void* ptr, void* user);
+  void* alloc_user;
+  void* stream;                /* cudaStream_t; NULL = legacy default stream */
+} lbm_config;
+
+typedef struct {
+  int kind;                    /* LBM_BC_* */
+  double beta;                 /* HRFD blend of Eq. 27 (0.28 calibrated) */
+  int ref_node;                /* bounce-back: 1 = B, 2 = F; HRFD requires 2 (F) */
+  double x_start;              /* walls: active where cell-centre x >= x_start;
+                                  cells before it behave as a symmetry plane */
+  double u_in[3];              /* inlet / free-stream velocity, m/s */
+  double nut_ratio_in;         /* inlet / free-stream nu_tilde / nu */
+} lbm_bc;
+
+typedef struct {
+  double mass;                 /* sum of populations (lattice units, rho0 = 1) */
+  double momentum[3];          /* sum of c_i f_i over the lattice (lattice units) */
+  double mean_u_tau[2];        /* m/s, mean over wall nodes of ymin / ymax */
+  double max_rel_du_tau;       /* max |u_tau - u_tau_prev| / u_tau over wall nodes since
+                                  the previous lbm_diagnostics call (Section 4.1.1 criterion) */
+  int nonfinite;               /* 1 if any population was NaN/Inf */
+  int newton_failures;         /* wall nodes where the Newton iteration hit its limit */
+} lbm_diag;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Create a solver for one lattice; all faces start periodic.  Validates the
+   configuration (tau > 1/2, sizes, enum values).  On success *out owns all
+   device state; on failure *out is NULL. */
+lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out);
+
+/* Set the condition of one face (LBM_XMIN..LBM_ZMAX) before the first
+   lbm_set_fields/lbm_step.  Rejects combinations the method does not define:
+   walls only on y faces, inlet only on xmin, outlet only on xmax, z periodic,
+   periodic faces paired, HRFD needs ny >= 3 (B, F, FF) per wall. */
+lbm_status lbm_set_bc(lbm_ctx* ctx, int face, const lbm_bc* bc);
+
+/* Initial state from physical fields rho (nz*ny*nx), u (3*nz*ny*nx), nu_tilde
+   (nz*ny*nx): post-collision populations f* = f^eq(rho, u) (Eq. 17), u^0 = u.
+   on_device != 0: the pointers are device memory; else host memory. */
+lbm_status lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* u,
+                          const double* nu_tilde, int on_device);
+
+/* Enqueue nsteps full steps (SA update, wall pre-pass, stream, face
+   conditions, HRFD wall reconstruction, moments, collision) on cfg.stream.
+   Steps are replayed from a captured CUDA graph. */
+lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Same steps launched without a graph, with CUDA events around every kernel;
+   kernel_ms[0] receives the total time of the bulk kernel, kernel_ms[1] of
+   the wall pre-pass kernel, summed over the nsteps (synchronises). */
+lbm_status lbm_step_timed(lbm_ctx* ctx, int nsteps, float kernel_ms[2]);
+
+/* Copy the fields selected by mask (LBM_FIELD_*) into caller buffers dst[k]
+   (float64, physical units), in increasing bit order.  dst_on_device != 0:
+   device pointers, else host pointers.  Synchronises cfg.stream and returns
+   LBM_ENONFINITE if the state holds NaN/Inf. */
+lbm_status lbm_fields(lbm_ctx* ctx, unsigned mask, void* const* dst, int dst_on_device);
+
+/* FP64 reductions over the lattice (deterministic order) into *out, host
+   memory.  Synchronises cfg.stream. */
+lbm_status lbm_diagnostics(lbm_ctx* ctx, lbm_diag* out);
+
+/* Raw state for checkpointing: the post-collision populations in storage
+   precision (bytes reported by lbm_state_bytes), the stored velocity and
+   nu_tilde in compute precision and u_tau in FP64, concatenated.  dst and src
+   are host buffers of lbm_state_bytes(ctx) bytes. */
+size_t lbm_state_bytes(const lbm_ctx* ctx);
+lbm_status lbm_get_state(lbm_ctx* ctx, void* dst);
+lbm_status lbm_set_state(lbm_ctx* ctx, const void* src);
+
+/* Release everything the context owns; NULL is allowed. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last failure of this context (static storage if ctx is NULL). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Lattice parameters after unit conversion: out[0] = dt (s), out[1] = nu
+   (lattice), out[2] = tau0, out[3..5] = F (lattice). */
+lbm_status lbm_lattice_params(const lbm_ctx* ctx, double out[6]);
+
+/* ------------------------------------------------------------------------
+ * Batched sweeps: many independent contexts advanced together by one
+ * persistent, cooperative kernel launch per lbm_batch_step call (captured in
+ * a CUDA graph).  Work items are (instance, tile) pairs; a bounded grid
+ * barrier separates the wall pre-pass and bulk phases of every step.
+ * Instances keep their own configurations and boundary conditions; the
+ * contexts must have been created and initialised (lbm_set_fields) first and
+ * must share one stream.  The batch does not own the contexts.
+ * ---------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** out);
+/* Advance every instance by nsteps; tiles_per_cta and threads are chosen by
+   the built-in autotuner on the first call unless lbm_batch_tune fixed them. */
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
+/* Time the candidate tile sizes / block sizes once and keep the fastest;
+   best[0] = threads per CTA, best[1] = cells per tile. */
+lbm_status lbm_batch_tune(lbm_batch* b, int best[2]);
+void lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

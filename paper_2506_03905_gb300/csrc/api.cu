@@ -1,0 +1,686 @@
+// api.cu -- host implementation of the C ABI declared in include/lbm.h.
+//
+// A context owns the double-buffered population, velocity and nu_tilde fields,
+// the per-wall-node state of both y faces and the FP64 reduction scratch.  A
+// step is two launches on the context stream: the wall pre-pass (k_wall) and
+// the fused bulk kernel (k_bulk); pairs of steps are captured once per buffer
+// parity into CUDA graphs and replayed by lbm_step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_ctx.h"
+#include "lbm_launch.h"
+
+using namespace lbm;
+
+static std::string g_static_error;
+
+void lbm_ctx_set_error(lbm_ctx* c, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_static_error = buf;
+}
+
+#define CUDA_TRY(ctx, expr)                                                            \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      lbm_ctx_set_error(ctx, "%s failed: %s", #expr, cudaGetErrorString(e_));          \
+      return LBM_ECUDA;                                                                \
+    }                                                                                  \
+  } while (0)
+
+static void* dalloc(lbm_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* ptr = nullptr;
+  if (c->cfg.alloc) {
+    ptr = c->cfg.alloc(bytes, c->cfg.alloc_user);
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    ptr = nullptr;
+  }
+  if (ptr) c->allocs.push_back(ptr);
+  return ptr;
+}
+
+// Device staging for host-side field transfers: allocated once (largest
+// request so far) through the context allocator and kept until destroy.
+static double* host_staging(lbm_ctx* c, size_t count) {
+  if (c->staging_count >= count) return c->staging;
+  if (c->staging) {
+    if (c->cfg.free) c->cfg.free(c->staging, c->cfg.alloc_user);
+    else if (!c->cfg.alloc) cudaFree(c->staging);
+    c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), (void*)c->staging), c->allocs.end());
+    c->staging = nullptr;
+    c->staging_count = 0;
+  }
+  c->staging = (double*)dalloc(c, count * sizeof(double));
+  if (c->staging) c->staging_count = count;
+  return c->staging;
+}
+
+static size_t storage_bytes(int st) {
+  switch (st) {
+    case LBM_FP32: return 4;
+    case LBM_FP16_SHIFTED:
+    case LBM_BF16_SHIFTED: return 2;
+    default: return 8;
+  }
+}
+
+static int to_dev_storage(int st) {
+  switch (st) {
+    case LBM_FP32: return ST_FP32;
+    case LBM_FP16_SHIFTED: return ST_FP16;
+    case LBM_BF16_SHIFTED: return ST_BF16;
+    default: return ST_FP64;
+  }
+}
+
+extern "C" const char* lbm_last_error(const lbm_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_static_error.c_str();
+}
+
+extern "C" lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (!cfg) {
+    lbm_ctx_set_error(nullptr, "cfg is NULL");
+    return LBM_EINVAL;
+  }
+  const lbm_config& k = *cfg;
+  if (k.lattice != LBM_D2Q9 && k.lattice != LBM_D3Q19) {
+    lbm_ctx_set_error(nullptr, "lattice must be LBM_D2Q9 or LBM_D3Q19");
+    return LBM_EINVAL;
+  }
+  if (k.nx < 1 || k.ny < 1 || k.nz < 1 || (k.lattice == LBM_D2Q9 && k.nz != 1)) {
+    lbm_ctx_set_error(nullptr, "bad sizes (D2Q9 needs nz == 1)");
+    return LBM_EINVAL;
+  }
+  if ((long long)k.nx * k.ny * k.nz > (1LL << 31)) {
+    lbm_ctx_set_error(nullptr, "lattice larger than 2^31 cells");
+    return LBM_EINVAL;
+  }
+  if (!(k.dx > 0) || !(k.nu > 0) || !(k.rho0 > 0) || !(k.u_ref > 0) || !(k.mach > 0)) {
+    lbm_ctx_set_error(nullptr, "dx, nu, rho0, u_ref and mach must be positive");
+    return LBM_EINVAL;
+  }
+  if (k.collision != LBM_BGK && k.collision != LBM_REGULARIZED) {
+    lbm_ctx_set_error(nullptr, "unknown collision");
+    return LBM_EINVAL;
+  }
+  if (k.storage < LBM_FP32 || k.storage > LBM_FP64) {
+    lbm_ctx_set_error(nullptr, "unknown storage");
+    return LBM_EINVAL;
+  }
+  if (k.turbulence != LBM_SA && k.turbulence != LBM_LAMINAR) {
+    lbm_ctx_set_error(nullptr, "unknown turbulence model");
+    return LBM_EINVAL;
+  }
+  if (k.wall_law != LBM_LAW_SA_ANALYTIC && k.wall_law != LBM_LAW_LOG) {
+    lbm_ctx_set_error(nullptr, "unknown wall law");
+    return LBM_EINVAL;
+  }
+  if (k.wall_law == LBM_LAW_LOG && !(k.kappa > 0)) {
+    lbm_ctx_set_error(nullptr, "log law needs kappa > 0");
+    return LBM_EINVAL;
+  }
+  lbm_ctx* c = new lbm_ctx();
+  c->cfg = k;
+  c->Q = k.lattice;
+  c->st = to_dev_storage(k.storage);
+  c->esz = storage_bytes(k.storage);
+  c->rsz = k.storage == LBM_FP64 ? 8 : 4;
+  c->nx = k.nx;
+  c->ny = k.ny;
+  c->nz = k.nz;
+  c->pitch = (k.nx + 7) / 8 * 8;
+  c->ncell = (long long)c->pitch * k.ny * k.nz;
+  c->ncells = (long long)k.nx * k.ny * k.nz;
+  // acoustic scaling (Section 4.1.1): dt = M dx / (sqrt(3) U_ref)
+  c->dt = k.mach * k.dx / (std::sqrt(3.0) * k.u_ref);
+  c->ucv = c->dt / k.dx;
+  c->nucv = c->dt / (k.dx * k.dx);
+  c->nu_lb = k.nu * c->nucv;
+  for (int a = 0; a < 3; ++a) c->F_lb[a] = k.force[a] * c->dt * c->dt / k.dx;
+  if (!(c->nu_lb > 0.0) || !(0.5 + 3.0 * c->nu_lb > 0.5)) {
+    lbm_ctx_set_error(nullptr, "tau0 = 1/2 + 3 nu_lb is not above 1/2 (nu_lb = %g)", c->nu_lb);
+    delete c;
+    return LBM_EINVAL;
+  }
+  for (int f = 0; f < 6; ++f) {
+    std::memset(&c->bc[f], 0, sizeof(lbm_bc));
+    c->bc[f].kind = LBM_BC_PERIODIC;
+    c->bc[f].beta = 0.28;
+    c->bc[f].ref_node = 2;
+    c->bc[f].x_start = -INFINITY;
+    c->bc[f].nut_ratio_in = 3.0;
+  }
+  c->stream = (cudaStream_t)k.stream;
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    lbm_ctx_set_error(nullptr, "cannot create capture stream: %s",
+                      cudaGetErrorString(cudaGetLastError()));
+    delete c;
+    return LBM_ECUDA;
+  }
+  bool ok = true;
+  for (int b = 0; b < 2; ++b) {
+    c->f[b] = dalloc(c, (size_t)c->Q * c->ncell * c->esz);
+    c->u[b] = dalloc(c, (size_t)3 * c->ncell * c->rsz);
+    c->nt[b] = dalloc(c, (size_t)c->ncell * c->rsz);
+    const size_t nodes = (size_t)k.nx * k.nz;
+    c->utau[b] = (double*)dalloc(c, nodes * sizeof(double));
+    c->uw[b] = dalloc(c, 3 * nodes * c->rsz);
+    c->rhow[b] = dalloc(c, nodes * c->rsz);
+    c->frec[b] = dalloc(c, (size_t)c->Q * nodes * c->rsz);
+    ok = ok && c->f[b] && c->u[b] && c->nt[b] && c->utau[b] && c->uw[b] && c->rhow[b] && c->frec[b];
+  }
+  c->utau_prev = (double*)dalloc(c, 2 * (size_t)k.nx * k.nz * sizeof(double));
+  c->flags = (unsigned*)dalloc(c, sizeof(unsigned) * 4);
+  c->red_blocks = 2 * 152;
+  c->red_chunk = (c->ncells + c->red_blocks - 1) / c->red_blocks;
+  c->partial = (double*)dalloc(c, (size_t)c->red_blocks * RED_VALS * sizeof(double));
+  c->red_out = (double*)dalloc(c, 16 * sizeof(double));
+  ok = ok && c->utau_prev && c->flags && c->partial && c->red_out;
+  if (!ok) {
+    lbm_destroy(c);
+    lbm_ctx_set_error(nullptr, "device allocation failed");
+    return LBM_ENOMEM;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_bc(lbm_ctx* c, int face, const lbm_bc* bc) {
+  if (!c || !bc) return LBM_EINVAL;
+  if (face < LBM_XMIN || face > LBM_ZMAX) {
+    lbm_ctx_set_error(c, "face %d out of range", face);
+    return LBM_EINVAL;
+  }
+  const int kd = bc->kind;
+  if (kd < LBM_BC_PERIODIC || kd > LBM_BC_FREESTREAM) {
+    lbm_ctx_set_error(c, "unknown boundary kind %d", kd);
+    return LBM_EINVAL;
+  }
+  const bool xf = face <= LBM_XMAX, yf = face == LBM_YMIN || face == LBM_YMAX;
+  const bool wall = kd == LBM_BC_WALL_SLIP_BB || kd == LBM_BC_WALL_HRFD;
+  if (face >= LBM_ZMIN && kd != LBM_BC_PERIODIC) {
+    lbm_ctx_set_error(c, "z faces must be periodic");
+    return LBM_EUNSUPPORTED;
+  }
+  if (xf && kd != LBM_BC_PERIODIC && kd != LBM_BC_INLET_ZOUHE && kd != LBM_BC_OUTLET_ZEROGRAD) {
+    lbm_ctx_set_error(c, "x faces take periodic, inlet or outlet conditions");
+    return LBM_EINVAL;
+  }
+  if ((kd == LBM_BC_INLET_ZOUHE && face != LBM_XMIN) ||
+      (kd == LBM_BC_OUTLET_ZEROGRAD && face != LBM_XMAX)) {
+    lbm_ctx_set_error(c, "inlet only on xmin, outlet only on xmax");
+    return LBM_EINVAL;
+  }
+  if (yf && (kd == LBM_BC_INLET_ZOUHE || kd == LBM_BC_OUTLET_ZEROGRAD)) {
+    lbm_ctx_set_error(c, "y faces take periodic, wall, symmetry or free-stream conditions");
+    return LBM_EINVAL;
+  }
+  if (wall && !(bc->ref_node == 1 || bc->ref_node == 2)) {
+    lbm_ctx_set_error(c, "ref_node must be 1 (B) or 2 (F)");
+    return LBM_EINVAL;
+  }
+  if (kd == LBM_BC_WALL_HRFD && bc->ref_node != 2) {
+    lbm_ctx_set_error(c, "HRFD takes its reference velocity at F (ref_node = 2)");
+    return LBM_EINVAL;
+  }
+  if (kd == LBM_BC_WALL_HRFD && !(bc->beta >= 0.0 && bc->beta <= 1.0)) {
+    lbm_ctx_set_error(c, "beta must lie in [0, 1]");
+    return LBM_EINVAL;
+  }
+  c->bc[face] = *bc;
+  c->finalized = false;
+  c->gvalid[0] = c->gvalid[1] = false;
+  return LBM_OK;
+}
+
+// Validate the face combination and build the kernel parameters.
+lbm_status lbm_ctx_finalize(lbm_ctx* c) {
+  if (c->finalized) return LBM_OK;
+  const lbm_config& k = c->cfg;
+  for (int ax = 0; ax < 3; ++ax) {
+    const bool a = c->bc[2 * ax].kind == LBM_BC_PERIODIC, b = c->bc[2 * ax + 1].kind == LBM_BC_PERIODIC;
+    if (a != b) {
+      lbm_ctx_set_error(c, "periodic faces must come in pairs (axis %d)", ax);
+      return LBM_EINVAL;
+    }
+  }
+  Params& p = c->base;
+  std::memset(&p, 0, sizeof(p));
+  p.nx = c->nx;
+  p.ny = c->ny;
+  p.nz = c->nz;
+  p.pitch = c->pitch;
+  p.ncell = c->ncell;
+  p.collision = k.collision;
+  p.turbulent = k.turbulence == LBM_SA;
+  p.wall_law = k.wall_law;
+  p.law_kappa = k.kappa;
+  p.law_B = k.B;
+  p.nu = c->nu_lb;
+  for (int a = 0; a < 3; ++a) p.F[a] = c->F_lb[a];
+  p.has_force = (p.F[0] != 0.0 || p.F[1] != 0.0 || p.F[2] != 0.0);
+  for (int f = 0; f < 6; ++f) p.kind[f] = c->bc[f].kind;
+  p.px = c->bc[LBM_XMIN].kind == LBM_BC_PERIODIC;
+  p.py = c->bc[LBM_YMIN].kind == LBM_BC_PERIODIC;
+  int nhrfd = 0;
+  for (int fi = 0; fi < 2; ++fi) {
+    const lbm_bc& b = c->bc[LBM_YMIN + fi];
+    const bool wall = b.kind == LBM_BC_WALL_SLIP_BB || b.kind == LBM_BC_WALL_HRFD;
+    p.wall[fi] = 0;
+    if (!wall) continue;
+    int x0 = 0;
+    while (x0 < c->nx && !(k.origin[0] + (x0 + 0.5) * k.dx >= b.x_start)) ++x0;
+    p.xw0[fi] = x0;
+    p.xs_lb[fi] = std::isfinite(b.x_start) ? (b.x_start - k.origin[0]) / k.dx : -1e30;
+    p.beta[fi] = b.beta;
+    p.ref_node[fi] = b.ref_node;
+    p.nwall[fi] = (c->nx - x0) * c->nz;
+    if (p.nwall[fi] > 0) p.wall[fi] = b.kind;
+    if (b.kind == LBM_BC_WALL_HRFD) ++nhrfd;
+    if (c->ny < 3) {
+      lbm_ctx_set_error(c, "walls need ny >= 3 (nodes B, F, FF)");
+      return LBM_EINVAL;
+    }
+    if (p.wall[fi] && x0 == 0 && c->bc[LBM_XMIN].kind == LBM_BC_INLET_ZOUHE) {
+      lbm_ctx_set_error(c, "a wall may not start at the inlet column");
+      return LBM_EINVAL;
+    }
+  }
+  if (nhrfd == 2 && c->ny < 6) {
+    lbm_ctx_set_error(c, "two HRFD walls need ny >= 6");
+    return LBM_EINVAL;
+  }
+  const int pf[4] = {LBM_XMIN, LBM_XMAX, LBM_YMIN, LBM_YMAX};
+  for (int j = 0; j < 4; ++j) {
+    const lbm_bc& b = c->bc[pf[j]];
+    for (int a = 0; a < 3; ++a) p.u_face[j][a] = b.u_in[a] * c->ucv;
+    p.nt_face[j] = b.nut_ratio_in * c->nu_lb;
+  }
+  if (c->bc[LBM_XMIN].kind == LBM_BC_INLET_ZOUHE && !(p.u_face[0][0] < 1.0)) {
+    lbm_ctx_set_error(c, "inlet velocity must be below one lattice speed");
+    return LBM_EINVAL;
+  }
+  for (int b = 0; b < 2; ++b) {
+    p.utau[b] = c->utau[b];
+    p.uw[b] = c->uw[b];
+    p.rhow[b] = c->rhow[b];
+    p.frec[b] = c->frec[b];
+  }
+  p.flags = c->flags;
+  c->finalized = true;
+  c->gvalid[0] = c->gvalid[1] = false;
+  return LBM_OK;
+}
+
+Params lbm_ctx_params(const lbm_ctx* c, int src) {
+  Params p = c->base;
+  p.f_src = c->f[src];
+  p.f_dst = c->f[1 - src];
+  p.u_src = c->u[src];
+  p.u_dst = c->u[1 - src];
+  p.nt_src = c->nt[src];
+  p.nt_dst = c->nt[1 - src];
+  return p;
+}
+
+void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, dim3* g, dim3* b) {
+  int bx = 32;
+  while (bx > 1 && bx / 2 >= c->nx) bx /= 2;
+  const int by = 256 / bx;
+  *b = dim3(bx, by, 1);
+  *g = dim3((c->nx + bx - 1) / bx, (c->ny + by - 1) / by, c->nz);
+}
+
+static void launch_step(lbm_ctx* c, int src, cudaStream_t s) {
+  const Params p = lbm_ctx_params(c, src);
+  const int maxw = (p.wall[0] ? p.nwall[0] : 0) > (p.wall[1] ? p.nwall[1] : 0)
+                       ? p.nwall[0] : (p.wall[1] ? p.nwall[1] : 0);
+  if (p.wall[0] || p.wall[1]) {
+    dim3 g((maxw + 127) / 128, 2, 1), b(128, 1, 1);
+    if (c->Q == 9) launch_wall_q9(c->st, p, g, b, s); else launch_wall_q19(c->st, p, g, b, s);
+  }
+  dim3 g, b;
+  lbm_ctx_bulk_launch_dims(c, &g, &b);
+  if (c->Q == 9) launch_bulk_q9(c->st, p, g, b, s); else launch_bulk_q19(c->st, p, g, b, s);
+}
+
+extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double* u,
+                                     const double* nu_tilde, int on_device) {
+  if (!c || !rho || !u || !nu_tilde) return LBM_EINVAL;
+  lbm_status s = lbm_ctx_finalize(c);
+  if (s != LBM_OK) return s;
+  const long long n = c->ncells;
+  const double *drho = rho, *du = u, *dnt = nu_tilde;
+  double* staging = nullptr;
+  if (!on_device) {
+    staging = host_staging(c, 5 * (size_t)n);
+    if (!staging) {
+      lbm_ctx_set_error(c, "staging allocation failed");
+      return LBM_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(staging, rho, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(staging + n, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(staging + 4 * n, nu_tilde, n * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream);
+    if (e != cudaSuccess) {
+      lbm_ctx_set_error(c, "upload failed: %s", cudaGetErrorString(e));
+      return LBM_ECUDA;
+    }
+    drho = staging;
+    du = staging + n;
+    dnt = staging + 4 * n;
+  }
+  Params p = lbm_ctx_params(c, 1 - c->cur);  // writes into buffer `cur`
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+  if (c->Q == 9)
+    launch_init_q9(c->st, p, grid, drho, du, dnt, c->cfg.rho0, c->ucv, c->nucv, c->stream);
+  else
+    launch_init_q19(c->st, p, grid, drho, du, dnt, c->cfg.rho0, c->ucv, c->nucv, c->stream);
+  for (int b = 0; b < 2; ++b)
+    CUDA_TRY(c, cudaMemsetAsync(c->utau[b], 0, (size_t)c->nx * c->nz * sizeof(double), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->utau_prev, 0, 2 * (size_t)c->nx * c->nz * sizeof(double), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * 4, c->stream));
+  CUDA_TRY(c, cudaGetLastError());
+  if (staging) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->ready = true;
+  return LBM_OK;
+}
+
+static lbm_status ensure_graph(lbm_ctx* c, int parity) {
+  if (c->gvalid[parity]) return LBM_OK;
+  if (c->gexec[parity]) {
+    cudaGraphExecDestroy(c->gexec[parity]);
+    c->gexec[parity] = nullptr;
+  }
+  CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  launch_step(c, parity, c->cap_stream);
+  launch_step(c, 1 - parity, c->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (e != cudaSuccess) {
+    lbm_ctx_set_error(c, "graph capture failed: %s", cudaGetErrorString(e));
+    return LBM_ECUDA;
+  }
+  e = cudaGraphInstantiate(&c->gexec[parity], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    lbm_ctx_set_error(c, "graph instantiate failed: %s", cudaGetErrorString(e));
+    return LBM_ECUDA;
+  }
+  c->gvalid[parity] = true;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step(lbm_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return LBM_EINVAL;
+  if (!c->ready) {
+    lbm_ctx_set_error(c, "lbm_set_fields (or lbm_set_state) must come first");
+    return LBM_EINVAL;
+  }
+  lbm_status s = lbm_ctx_finalize(c);
+  if (s != LBM_OK) return s;
+  int left = nsteps;
+  if (left >= 2) {
+    s = ensure_graph(c, c->cur);
+    if (s != LBM_OK) return s;
+    while (left >= 2) {
+      CUDA_TRY(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
+      left -= 2;
+    }
+  }
+  if (left == 1) {
+    launch_step(c, c->cur, c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    c->cur ^= 1;
+  }
+  c->steps_done += nsteps;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int nsteps, float kernel_ms[2]) {
+  if (!c || nsteps < 0 || !kernel_ms) return LBM_EINVAL;
+  if (!c->ready) {
+    lbm_ctx_set_error(c, "lbm_set_fields (or lbm_set_state) must come first");
+    return LBM_EINVAL;
+  }
+  lbm_status s = lbm_ctx_finalize(c);
+  if (s != LBM_OK) return s;
+  std::vector<cudaEvent_t> ev(3 * (size_t)nsteps);
+  for (auto& e : ev) CUDA_TRY(c, cudaEventCreate(&e));
+  for (int k = 0; k < nsteps; ++k) {
+    const Params p = lbm_ctx_params(c, c->cur);
+    CUDA_TRY(c, cudaEventRecord(ev[3 * k], c->stream));
+    if (p.wall[0] || p.wall[1]) {
+      const int maxw = std::max(p.wall[0] ? p.nwall[0] : 0, p.wall[1] ? p.nwall[1] : 0);
+      dim3 g((maxw + 127) / 128, 2, 1), b(128, 1, 1);
+      if (c->Q == 9) launch_wall_q9(c->st, p, g, b, c->stream);
+      else launch_wall_q19(c->st, p, g, b, c->stream);
+    }
+    CUDA_TRY(c, cudaEventRecord(ev[3 * k + 1], c->stream));
+    dim3 g, b;
+    lbm_ctx_bulk_launch_dims(c, &g, &b);
+    if (c->Q == 9) launch_bulk_q9(c->st, p, g, b, c->stream);
+    else launch_bulk_q19(c->st, p, g, b, c->stream);
+    CUDA_TRY(c, cudaEventRecord(ev[3 * k + 2], c->stream));
+    c->cur ^= 1;
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  float wall = 0.f, bulk = 0.f;
+  for (int k = 0; k < nsteps; ++k) {
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, ev[3 * k], ev[3 * k + 1]);
+    cudaEventElapsedTime(&b, ev[3 * k + 1], ev[3 * k + 2]);
+    wall += a;
+    bulk += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  kernel_ms[0] = bulk;
+  kernel_ms[1] = wall;
+  c->steps_done += nsteps;
+  return LBM_OK;
+}
+
+static lbm_status check_flags(lbm_ctx* c) {
+  unsigned h[4] = {0, 0, 0, 0};
+  CUDA_TRY(c, cudaMemcpyAsync(h, c->flags, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->last_flags = h[0];
+  if (h[0] & FLAG_NONFINITE) {
+    lbm_ctx_set_error(c, "non-finite value in the state");
+    return LBM_ENONFINITE;
+  }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_fields(lbm_ctx* c, unsigned mask, void* const* dst, int dst_on_device) {
+  if (!c || (mask && !dst)) return LBM_EINVAL;
+  if (!c->ready) {
+    lbm_ctx_set_error(c, "no state yet");
+    return LBM_EINVAL;
+  }
+  if (mask & ~0xFFu) {
+    lbm_ctx_set_error(c, "unknown field bits in mask");
+    return LBM_EINVAL;
+  }
+  const long long n = c->ncells;
+  const Params p = lbm_ctx_params(c, c->cur);
+  const double vel = c->cfg.dx / c->dt, visc = c->cfg.dx * c->cfg.dx / c->dt;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+  int slot = 0;
+  double* tmp = nullptr;
+  for (int bit = 0; bit < 4; ++bit) {
+    if (!(mask & (1u << bit))) continue;
+    const size_t count = (bit == 1 ? 3 : 1) * (size_t)n;
+    double* out = (double*)dst[slot++];
+    if (!out) return LBM_EINVAL;
+    double* target = out;
+    if (!dst_on_device) {
+      if (!tmp) tmp = host_staging(c, 3 * (size_t)n);
+      if (!tmp) {
+        lbm_ctx_set_error(c, "staging allocation failed");
+        return LBM_ENOMEM;
+      }
+      target = tmp;
+    }
+    double* a[4] = {nullptr, nullptr, nullptr, nullptr};
+    a[bit] = target;
+    if (c->Q == 9)
+      launch_fields_q9(c->st, p, grid, a[0], a[1], a[2], a[3], c->cfg.rho0, vel, visc, c->stream);
+    else
+      launch_fields_q19(c->st, p, grid, a[0], a[1], a[2], a[3], c->cfg.rho0, vel, visc, c->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !dst_on_device)
+      e = cudaMemcpyAsync(out, tmp, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      lbm_ctx_set_error(c, "field export failed: %s", cudaGetErrorString(e));
+      return LBM_ECUDA;
+    }
+  }
+  // wall-node arrays: u_tau and C_f = 2 (u_tau / U_ref)^2 on the (z, x) grid of each y face
+  if (mask & 0xF0u) {
+    const size_t nodes = (size_t)c->nx * c->nz;
+    std::vector<double> ut(nodes), full(nodes);
+    for (int bit = 4; bit < 8; ++bit) {
+      if (!(mask & (1u << bit))) continue;
+      const int fi = (bit - 4) & 1;
+      const bool cf = bit >= 6;
+      std::fill(full.begin(), full.end(), 0.0);
+      if (c->base.wall[fi]) {
+        const int nw = c->base.nwall[fi];
+        CUDA_TRY(c, cudaMemcpyAsync(ut.data(), c->utau[fi], nw * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        const int x0 = c->base.xw0[fi], nwx = c->nx - x0;
+        for (int m = 0; m < nw; ++m) {
+          const int z = m / nwx, x = x0 + m % nwx;
+          const double v = ut[m] * vel;
+          full[(size_t)z * c->nx + x] = cf ? 2.0 * (v / c->cfg.u_ref) * (v / c->cfg.u_ref) : v;
+        }
+      }
+      double* out = (double*)dst[slot++];
+      if (!out) return LBM_EINVAL;
+      if (dst_on_device)
+        CUDA_TRY(c, cudaMemcpyAsync(out, full.data(), nodes * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream));
+      else
+        std::memcpy(out, full.data(), nodes * sizeof(double));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+  }
+  return check_flags(c);
+}
+
+extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out) {
+  if (!c || !out) return LBM_EINVAL;
+  if (!c->ready) {
+    lbm_ctx_set_error(c, "no state yet");
+    return LBM_EINVAL;
+  }
+  const Params p = lbm_ctx_params(c, c->cur);
+  if (c->Q == 9) launch_reduce_q9(c->st, p, c->red_blocks, c->partial, c->red_chunk, c->stream);
+  else launch_reduce_q19(c->st, p, c->red_blocks, c->partial, c->red_chunk, c->stream);
+  launch_reduce_final(c->partial, c->red_blocks, c->red_out, c->stream);
+  launch_wall_stats(p, c->utau_prev, c->red_out + 8, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  double h[16];
+  CUDA_TRY(c, cudaMemcpyAsync(h, c->red_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  lbm_status s = check_flags(c);
+  const double vel = c->cfg.dx / c->dt;
+  out->mass = h[0];
+  out->momentum[0] = h[1];
+  out->momentum[1] = h[2];
+  out->momentum[2] = h[3];
+  out->mean_u_tau[0] = h[8] * vel;
+  out->mean_u_tau[1] = h[9] * vel;
+  out->max_rel_du_tau = h[10];
+  out->nonfinite = (c->last_flags & FLAG_NONFINITE) ? 1 : 0;
+  out->newton_failures = (c->last_flags & FLAG_NEWTON) ? 1 : 0;
+  return s == LBM_ENONFINITE ? LBM_OK : s;
+}
+
+extern "C" size_t lbm_state_bytes(const lbm_ctx* c) {
+  if (!c) return 0;
+  return (size_t)c->Q * c->ncell * c->esz + (size_t)4 * c->ncell * c->rsz +
+         2 * (size_t)c->nx * c->nz * sizeof(double);
+}
+
+extern "C" lbm_status lbm_get_state(lbm_ctx* c, void* dst) {
+  if (!c || !dst) return LBM_EINVAL;
+  if (!c->ready) {
+    lbm_ctx_set_error(c, "no state yet");
+    return LBM_EINVAL;
+  }
+  char* o = (char*)dst;
+  const size_t fb = (size_t)c->Q * c->ncell * c->esz, ub = 3 * (size_t)c->ncell * c->rsz,
+               nb = (size_t)c->ncell * c->rsz, wb = (size_t)c->nx * c->nz * sizeof(double);
+  CUDA_TRY(c, cudaMemcpyAsync(o, c->f[c->cur], fb, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(o + fb, c->u[c->cur], ub, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(o + fb + ub, c->nt[c->cur], nb, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(o + fb + ub + nb, c->utau[0], wb, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(o + fb + ub + nb + wb, c->utau[1], wb, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_state(lbm_ctx* c, const void* src) {
+  if (!c || !src) return LBM_EINVAL;
+  lbm_status s = lbm_ctx_finalize(c);
+  if (s != LBM_OK) return s;
+  const char* o = (const char*)src;
+  const size_t fb = (size_t)c->Q * c->ncell * c->esz, ub = 3 * (size_t)c->ncell * c->rsz,
+               nb = (size_t)c->ncell * c->rsz, wb = (size_t)c->nx * c->nz * sizeof(double);
+  CUDA_TRY(c, cudaMemcpyAsync(c->f[c->cur], o, fb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->u[c->cur], o + fb, ub, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->nt[c->cur], o + fb + ub, nb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->utau[0], o + fb + ub + nb, wb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->utau[1], o + fb + ub + nb + wb, wb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * 4, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->ready = true;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_lattice_params(const lbm_ctx* c, double out[6]) {
+  if (!c || !out) return LBM_EINVAL;
+  out[0] = c->dt;
+  out[1] = c->nu_lb;
+  out[2] = 0.5 + 3.0 * c->nu_lb;
+  out[3] = c->F_lb[0];
+  out[4] = c->F_lb[1];
+  out[5] = c->F_lb[2];
+  return LBM_OK;
+}
+
+extern "C" void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (int p = 0; p < 2; ++p)
+    if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
+  for (void* ptr : c->allocs) {
+    if (c->cfg.free) c->cfg.free(ptr, c->cfg.alloc_user);
+    else if (!c->cfg.alloc) cudaFree(ptr);
+  }
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}

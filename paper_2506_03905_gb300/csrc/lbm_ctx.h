@@ -1,0 +1,53 @@
+// lbm_ctx.h -- the context object behind the opaque lbm_ctx handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_device.cuh"
+
+struct lbm_ctx {
+  lbm_config cfg;
+  lbm_bc bc[6];
+  int Q = 0, st = 0;
+  size_t esz = 4, rsz = 4;         // storage / compute element size
+  int nx = 0, ny = 0, nz = 0, pitch = 0;
+  long long ncell = 0;             // padded cells (pitch * ny * nz)
+  long long ncells = 0;            // cells (nx * ny * nz)
+  double dt = 0, ucv = 0, nucv = 0, nu_lb = 0;
+  double F_lb[3] = {0, 0, 0};
+  cudaStream_t stream = nullptr;   // caller's stream
+  cudaStream_t cap_stream = nullptr;
+  void* f[2] = {nullptr, nullptr};
+  void* u[2] = {nullptr, nullptr};
+  void* nt[2] = {nullptr, nullptr};
+  double* utau[2] = {nullptr, nullptr};
+  void* uw[2] = {nullptr, nullptr};
+  void* rhow[2] = {nullptr, nullptr};
+  void* frec[2] = {nullptr, nullptr};
+  double* utau_prev = nullptr;
+  unsigned* flags = nullptr;
+  unsigned last_flags = 0;
+  double* partial = nullptr;       // FP64 reduction scratch: red_blocks * RED_VALS
+  int red_blocks = 0;
+  long long red_chunk = 0;
+  double* red_out = nullptr;
+  double* staging = nullptr;       // device staging of host transfers (doubles)
+  size_t staging_count = 0;
+  int cur = 0;                     // buffer holding the current state
+  bool ready = false;
+  bool finalized = false;
+  long long steps_done = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  bool gvalid[2] = {false, false};
+  lbm::Params base;
+  std::string err;
+  std::vector<void*> allocs;
+};
+
+void lbm_ctx_set_error(lbm_ctx* c, const char* fmt, ...);
+lbm_status lbm_ctx_finalize(lbm_ctx* c);
+lbm::Params lbm_ctx_params(const lbm_ctx* c, int src);
+void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, dim3* g, dim3* b);

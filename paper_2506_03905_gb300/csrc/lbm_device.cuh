@@ -1,0 +1,526 @@
+// lbm_device.cuh -- device-side building blocks of the LBM-RANS step.
+//
+// Lattice units throughout (dx = dt = 1, c_s^2 = 1/3).  Populations are stored
+// as shifted deviations g_i = f_i - w_i (rho0 = 1) in the storage type, and all
+// arithmetic runs in the compute type R (float, or double for the FP64 mode).
+//
+// Memory layout (structure of arrays, x fastest, rows padded to `pitch`):
+//   f[q][z][y][x]  -> f[q * ncell + (z*ny + y)*pitch + x]
+//   u[c][z][y][x]  -> u[c * ncell + ...]      (velocity of the previous step)
+//   nt[z][y][x]                               (SA working variable)
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+enum BcKind {
+  BC_PERIODIC = 0, BC_WALL_BB = 1, BC_WALL_HRFD = 2, BC_SYMMETRY = 3,
+  BC_INLET = 4, BC_OUTLET = 5, BC_FREESTREAM = 6
+};
+enum { XMIN = 0, XMAX = 1, YMIN = 2, YMAX = 3 };
+enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2, ST_FP64 = 3 };
+enum { FLAG_NONFINITE = 1u, FLAG_NEWTON = 2u };
+constexpr int RED_THREADS = 256;   // FP64 reduction block size
+constexpr int RED_VALS = 4;        // mass, momentum x/y/z
+
+// --------------------------------------------------------------------------
+// Velocity sets.  D2Q9: rest, 4 axis, 4 diagonal.  D3Q19: rest, 6 axis, 12
+// edge diagonals.  Directions 2k-1 and 2k are opposite (k >= 1).
+// --------------------------------------------------------------------------
+template <int Q> struct Lat;
+
+template <> struct Lat<9> {
+  static constexpr int Q = 9, D = 2;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    constexpr int t[9][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                             {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+    return t[i][a];
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  // index of the direction with c_y negated
+  __host__ __device__ static constexpr int my(int i) {
+    constexpr int t[9] = {0, 1, 2, 4, 3, 7, 8, 5, 6};
+    return t[i];
+  }
+};
+
+template <> struct Lat<19> {
+  static constexpr int Q = 19, D = 3;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    constexpr int t[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                              {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                              {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                              {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return t[i][a];
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr int my(int i) {
+    constexpr int t[19] = {0, 1, 2, 4, 3, 5, 6, 9, 10, 7, 8, 11, 12, 13, 14, 18, 17, 16, 15};
+    return t[i];
+  }
+};
+
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// --------------------------------------------------------------------------
+// Storage codecs: shifted deviation g = f - w in the storage type.
+// FP16 values are kept multiplied by 2^12 so that deviations down to ~1e-8
+// stay in the normal range (|g| < 16 is always representable).
+// --------------------------------------------------------------------------
+template <int ST> struct Codec;
+template <> struct Codec<ST_FP32> {
+  using T = float;
+  __device__ static __forceinline__ float ld(const T* p) { return *p; }
+  __device__ static __forceinline__ void st(T* p, float v) { *p = v; }
+};
+template <> struct Codec<ST_FP64> {
+  using T = double;
+  __device__ static __forceinline__ double ld(const T* p) { return *p; }
+  __device__ static __forceinline__ void st(T* p, double v) { *p = v; }
+};
+template <> struct Codec<ST_FP16> {
+  using T = __half;
+  __device__ static __forceinline__ float ld(const T* p) { return __half2float(*p) * (1.0f / 4096.0f); }
+  __device__ static __forceinline__ void st(T* p, float v) { *p = __float2half_rn(v * 4096.0f); }
+};
+template <> struct Codec<ST_BF16> {
+  using T = __nv_bfloat16;
+  __device__ static __forceinline__ float ld(const T* p) { return __bfloat162float(*p); }
+  __device__ static __forceinline__ void st(T* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <int ST> struct Compute { using R = float; };
+template <> struct Compute<ST_FP64> { using R = double; };
+
+// --------------------------------------------------------------------------
+// Kernel parameters (lattice units), passed by value.
+// --------------------------------------------------------------------------
+struct Params {
+  int nx, ny, nz, pitch;
+  long long ncell;             // pitch * ny * nz: stride between directions / components
+  int collision;               // 0 BGK, 1 regularized
+  int turbulent;               // 1: SA active
+  int wall_law;                // 0 Eq. 16, 1 log law
+  int has_force;
+  double nu;                   // molecular viscosity (lattice)
+  double F[3];                 // body force density (lattice)
+  double law_kappa, law_B;
+  int kind[6];                 // face kinds
+  int px, py;                  // x / y periodic
+  // y faces, index 0 = ymin, 1 = ymax
+  int wall[2];                 // 0 or BC_WALL_BB / BC_WALL_HRFD
+  int xw0[2];                  // first wall column (columns before it are symmetry)
+  double xs_lb[2];             // leading edge position in lattice units from the x face
+  double beta[2];
+  int ref_node[2];
+  int nwall[2];                // (nx - xw0) * nz wall nodes
+  double u_face[4][3];         // prescribed velocity of xmin, xmax, ymin, ymax
+  double nt_face[4];           // prescribed nu_tilde of xmin, xmax, ymin, ymax
+  // state
+  const void* f_src;
+  void* f_dst;
+  const void* u_src;
+  void* u_dst;
+  const void* nt_src;
+  void* nt_dst;
+  double* utau[2];             // per wall node, FP64 (also the Newton warm start)
+  void* uw[2];                 // BB: slip velocity (3 per node), compute type
+  void* rhow[2];               // BB: wall density, compute type
+  void* frec[2];               // HRFD: rebuilt populations (Q per node), deviations, compute type
+  unsigned* flags;
+};
+
+__device__ __forceinline__ long long cidx(const Params& p, int x, int y, int z) {
+  return ((long long)z * p.ny + y) * p.pitch + x;
+}
+
+// --------------------------------------------------------------------------
+// Spalart-Allmaras model (Section 2.2, Eqs. 10-14) and its stencil.
+// --------------------------------------------------------------------------
+struct SAConst {
+  static constexpr double cb1 = 0.1355, cb2 = 0.622, sigma = 2.0 / 3.0, kappa = 0.41;
+  static constexpr double cw2 = 0.3, cw3 = 2.0, cv1 = 7.1, rlim = 10.0;
+  static constexpr double cv2lim = 0.7, cv3lim = 0.9;
+};
+
+template <class R> __device__ __forceinline__ R sa_fv1(R chi) {
+  const R c3 = chi * chi * chi;
+  const R cv = (R)SAConst::cv1;
+  return c3 / (c3 + cv * cv * cv);
+}
+
+// nu_t = nu_tilde f_v1(nu_tilde / nu) (Eq. 10)
+template <class R> __device__ __forceinline__ R sa_nut(R nt, R nu) { return nt * sa_fv1<R>(nt / nu); }
+
+// P - D of Eq. 12 with S~ (Eq. 13, kept positive by the ICCFD7 limiter) and r, f_w (Eq. 14)
+template <class R> __device__ __forceinline__ R sa_source(R nt, R S, R nu, R inv_d2) {
+  const R kap = (R)SAConst::kappa;
+  const R cw1 = (R)SAConst::cb1 / (kap * kap) + ((R)1 + (R)SAConst::cb2) / (R)SAConst::sigma;
+  const R chi = nt / nu;
+  const R fv1 = sa_fv1<R>(chi);
+  const R fv2 = (R)1 - chi / ((R)1 + chi * fv1);
+  const R inv_kd2 = inv_d2 / (kap * kap);
+  const R sbar = nt * fv2 * inv_kd2;
+  R st;
+  if (sbar >= -(R)SAConst::cv2lim * S) {
+    st = S + sbar;
+  } else {
+    st = S + S * ((R)(SAConst::cv2lim * SAConst::cv2lim) * S + (R)SAConst::cv3lim * sbar) /
+                 (((R)SAConst::cv3lim - (R)2 * (R)SAConst::cv2lim) * S - sbar);
+  }
+  R r = (R)SAConst::rlim;
+  if (st > (R)0) {
+    const R q = nt * inv_kd2 / st;
+    r = q < r ? q : r;
+  }
+  const R r2 = r * r, r6 = r2 * r2 * r2;
+  const R g = r + (R)SAConst::cw2 * (r6 - r);
+  const R g2 = g * g, g6 = g2 * g2 * g2;
+  const R cw36 = (R)64;  // c_w3^6
+  const R fw = g * pow(((R)1 + cw36) / (g6 + cw36), (R)(1.0 / 6.0));
+  return (R)SAConst::cb1 * st * nt - cw1 * fw * nt * nt * inv_d2;
+}
+
+// Neighbour nu_tilde and velocity with the face ghost rules of the SA stencil:
+// periodic wrap; symmetry and wall faces mirror (normal velocity negated);
+// inlet and free-stream faces the prescribed state; outlet zero gradient.
+template <class R> struct Nb {
+  R nt;
+  R u[3];
+};
+
+template <class R>
+__device__ __forceinline__ Nb<R> load_nb(const Params& p, const R* __restrict__ nt,
+                                         const R* __restrict__ u, int x, int y, int z) {
+  Nb<R> n;
+  const long long id = cidx(p, x, y, z);
+  n.nt = nt[id];
+  n.u[0] = u[id];
+  n.u[1] = u[id + p.ncell];
+  n.u[2] = u[id + 2 * p.ncell];
+  return n;
+}
+
+template <class R>
+__device__ Nb<R> neighbour(const Params& p, const R* __restrict__ nt, const R* __restrict__ u,
+                           int x, int y, int z, int axis, int s) {
+  if (axis == 0) {
+    int xn = x + s;
+    if (xn >= 0 && xn < p.nx) return load_nb<R>(p, nt, u, xn, y, z);
+    if (p.px) return load_nb<R>(p, nt, u, xn < 0 ? xn + p.nx : xn - p.nx, y, z);
+    const int f = xn < 0 ? XMIN : XMAX;
+    const int k = p.kind[f];
+    if (k == BC_OUTLET) return load_nb<R>(p, nt, u, x, y, z);
+    Nb<R> n;  // inlet (and any prescribed face)
+    n.nt = (R)p.nt_face[f];
+    n.u[0] = (R)p.u_face[f][0];
+    n.u[1] = (R)p.u_face[f][1];
+    n.u[2] = (R)p.u_face[f][2];
+    return n;
+  }
+  if (axis == 1) {
+    int yn = y + s;
+    if (yn >= 0 && yn < p.ny) return load_nb<R>(p, nt, u, x, yn, z);
+    if (p.py) return load_nb<R>(p, nt, u, x, yn < 0 ? yn + p.ny : yn - p.ny, z);
+    const int f = yn < 0 ? YMIN : YMAX;
+    const int k = p.kind[f];
+    if (k == BC_FREESTREAM) {
+      Nb<R> n;
+      n.nt = (R)p.nt_face[f];
+      n.u[0] = (R)p.u_face[f][0];
+      n.u[1] = (R)p.u_face[f][1];
+      n.u[2] = (R)p.u_face[f][2];
+      return n;
+    }
+    Nb<R> n = load_nb<R>(p, nt, u, x, y, z);  // mirror
+    n.u[1] = -n.u[1];
+    return n;
+  }
+  int zn = z + s;
+  zn = zn < 0 ? zn + p.nz : (zn >= p.nz ? zn - p.nz : zn);
+  return load_nb<R>(p, nt, u, x, y, zn);
+}
+
+template <class R> __device__ __forceinline__ R inv_wall_dist2(const Params& p, int x, int y) {
+  R d2 = (R)3.0e38;
+  bool any = false;
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    if (p.wall[f]) {
+      const R dy = f == 0 ? (R)y + (R)0.5 : (R)(p.ny - y) - (R)0.5;
+      R e = dy * dy;
+      if (x < p.xw0[f]) {
+        const R dxl = ((R)x + (R)0.5) - (R)p.xs_lb[f];
+        e += dxl * dxl;
+      }
+      d2 = e < d2 ? e : d2;
+      any = true;
+    }
+  }
+  return any ? (R)1 / d2 : (R)0;
+}
+
+// Explicit Euler update of Eq. 11 at one cell, clipped at zero.
+template <class R, bool THREE_D>
+__device__ R sa_update(const Params& p, const R* __restrict__ nt, const R* __restrict__ u, int x,
+                       int y, int z) {
+  const Nb<R> c = load_nb<R>(p, nt, u, x, y, z);
+  const R nu = (R)p.nu;
+  Nb<R> m[3], pl[3];
+  m[0] = neighbour<R>(p, nt, u, x, y, z, 0, -1);
+  pl[0] = neighbour<R>(p, nt, u, x, y, z, 0, +1);
+  m[1] = neighbour<R>(p, nt, u, x, y, z, 1, -1);
+  pl[1] = neighbour<R>(p, nt, u, x, y, z, 1, +1);
+  if (THREE_D) {
+    m[2] = neighbour<R>(p, nt, u, x, y, z, 2, -1);
+    pl[2] = neighbour<R>(p, nt, u, x, y, z, 2, +1);
+  } else {
+    m[2] = c;
+    pl[2] = c;
+  }
+  const R h = (R)0.5;
+  // vorticity by central differences of the previous-step velocity
+  const R wx = h * (pl[1].u[2] - m[1].u[2]) - h * (pl[2].u[1] - m[2].u[1]);
+  const R wy = h * (pl[2].u[0] - m[2].u[0]) - h * (pl[0].u[2] - m[0].u[2]);
+  const R wz = h * (pl[0].u[1] - m[0].u[1]) - h * (pl[1].u[0] - m[1].u[0]);
+  const R S = sqrt(wx * wx + wy * wy + wz * wz);
+  R conv = 0, diff = 0, grad2 = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R ua = c.u[a];
+    conv += ua > (R)0 ? ua * (c.nt - m[a].nt) : ua * (pl[a].nt - c.nt);
+    diff += (nu + h * (c.nt + pl[a].nt)) * (pl[a].nt - c.nt) -
+            (nu + h * (c.nt + m[a].nt)) * (c.nt - m[a].nt);
+    const R g = h * (pl[a].nt - m[a].nt);
+    grad2 += g * g;
+  }
+  const R inv_d2 = inv_wall_dist2<R>(p, x, y);
+  const R rhs = -conv + sa_source<R>(c.nt, S, nu, inv_d2) +
+                (diff + (R)SAConst::cb2 * grad2) / (R)SAConst::sigma;
+  const R nn = c.nt + rhs;
+  return nn > (R)0 ? nn : (R)0;
+}
+
+// --------------------------------------------------------------------------
+// Wall functions (Eqs. 15-16, log law) and the FP64 u_tau inversion.
+// Eq. 16 is evaluated on its continuous branch, atan2(b, y+ + a).
+// --------------------------------------------------------------------------
+struct WF {
+  static constexpr double kappa = 0.41, cv1 = 7.1;
+  static constexpr double Bb = 5.033908790505579, a1 = 8.148221580024245,
+                          a2 = -6.9287093849022945, b1 = 7.4600876082527945,
+                          b2 = 7.468145790401841, c1 = 2.5496773539754747,
+                          c2 = 1.3301651588535228, c3 = 3.599459109332379,
+                          c4 = 3.639753186868684494;
+};
+
+__host__ __device__ inline double wf_uplus(int law, double kap, double B, double yp) {
+  if (law == 1) return log(yp) / kap + B;
+  const double s1 = yp + WF::a1, s2 = yp + WF::a2;
+  return WF::Bb + WF::c1 * log(s1 * s1 + WF::b1 * WF::b1) - WF::c2 * log(s2 * s2 + WF::b2 * WF::b2) -
+         WF::c3 * atan2(WF::b1, s1) - WF::c4 * atan2(WF::b2, s2);
+}
+
+__host__ __device__ inline double wf_dudy(int law, double kap, double yp) {
+  if (law == 1) return 1.0 / (kap * yp);
+  const double ky = WF::kappa * yp, ky3 = ky * ky * ky, cv3 = WF::cv1 * WF::cv1 * WF::cv1;
+  return (cv3 + ky3) / (cv3 + (1.0 + ky) * ky3);
+}
+
+// Solve U = u u+(u y / nu) for u >= 0.  Newton steps inside a sign-change
+// bracket, bisection when a step leaves it; stops at a relative step below
+// 1e-15.  Returns false if the iteration limit was reached.
+__host__ __device__ inline bool solve_utau(int law, double kap, double B, double U, double y,
+                                           double nu, double guess, double* out) {
+  if (!(U > 0.0)) {
+    *out = 0.0;
+    return true;
+  }
+  double lo = 0.0, hi = fmax(U, sqrt(U * nu / y));
+  for (int k = 0; k < 400; ++k) {
+    const double yp = hi * y / nu;
+    if (hi * wf_uplus(law, kap, B, yp) - U > 0.0) break;
+    hi *= 2.0;
+  }
+  double x = (guess > lo && guess < hi) ? guess : 0.5 * (lo + hi);
+  for (int it = 0; it < 200; ++it) {
+    const double yp = x * y / nu;
+    const double up = wf_uplus(law, kap, B, yp);
+    const double g = x * up - U;
+    if (g == 0.0) {
+      *out = x;
+      return true;
+    }
+    if (g < 0.0) lo = x; else hi = x;
+    const double dg = up + yp * wf_dudy(law, kap, yp);
+    double xn = x - g / dg;
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    if (fabs(xn - x) <= 1e-15 * fabs(xn)) {
+      *out = xn;
+      return true;
+    }
+    x = xn;
+  }
+  *out = x;
+  return false;
+}
+
+// --------------------------------------------------------------------------
+// Post-stream populations with the face rules (Eq. 3 with Eq. 31, symmetry,
+// free stream, zero-gradient outlet).  Returns the deviation g_i at
+// (x, y, z) after streaming; `known` is false for Zou-He inlet unknowns and
+// for HRFD wall unknowns, whose value is replaced later.
+// --------------------------------------------------------------------------
+template <int Q, int ST>
+__device__ typename Compute<ST>::R pull_bc(const Params& p, int x, int y, int z, int i, bool* known) {
+  using L = Lat<Q>;
+  using C = Codec<ST>;
+  using R = typename Compute<ST>::R;
+  using T = typename C::T;
+  const T* __restrict__ f = (const T*)p.f_src;
+  *known = true;
+  const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+  int sx = x - cx;
+  if (sx < 0 || sx >= p.nx) {
+    if (p.px) {
+      sx = sx < 0 ? sx + p.nx : sx - p.nx;
+    } else if (sx < 0) {
+      *known = false;  // inlet unknown: Zou-He
+      return (R)0;
+    } else {
+      // zero-gradient outlet: the post-stream value of the neighbouring column
+      x -= 1;
+      sx = x - cx;
+    }
+  }
+  int sz = z - cz;
+  sz = sz < 0 ? sz + p.nz : (sz >= p.nz ? sz - p.nz : sz);
+  int sy = y - cy;
+  if (sy >= 0 && sy < p.ny) return (R)C::ld(f + i * p.ncell + cidx(p, sx, sy, sz));
+  if (p.py) {
+    sy = sy < 0 ? sy + p.ny : sy - p.ny;
+    return (R)C::ld(f + i * p.ncell + cidx(p, sx, sy, sz));
+  }
+  const int fi = sy < 0 ? 0 : 1;   // 0 = ymin, 1 = ymax
+  const int kind = p.kind[YMIN + fi];
+  if (kind == BC_FREESTREAM) {
+    const R ux = (R)p.u_face[YMIN + fi][0], uy = (R)p.u_face[YMIN + fi][1],
+            uz = (R)p.u_face[YMIN + fi][2];
+    const R cu = (R)cx * ux + (R)cy * uy + (R)cz * uz;
+    const R uu = ux * ux + uy * uy + uz * uz;
+    return (R)L::w(i) * ((R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
+  }
+  const bool wall_col = p.wall[fi] && x >= p.xw0[fi];
+  if (wall_col && kind == BC_WALL_BB) {
+    // Eq. 31: f_i(B, t+1) = f*_{opp i}(B, t) + 2 w rho_w c_i.u_w / c_s^2
+    const int node = z * (p.nx - p.xw0[fi]) + (x - p.xw0[fi]);
+    const R* uw = (const R*)p.uw[fi] + 3 * node;
+    const R cu = (R)cx * uw[0] + (R)cy * uw[1] + (R)cz * uw[2];
+    const R rw = ((const R*)p.rhow[fi])[node];
+    return (R)C::ld(f + opp(i) * p.ncell + cidx(p, x, y, z)) + (R)6 * (R)L::w(i) * rw * cu;
+  }
+  if (wall_col) {  // HRFD: every population of B is rebuilt later
+    *known = false;
+    return (R)0;
+  }
+  // symmetry: specular reflection from the same row
+  return (R)C::ld(f + L::my(i) * p.ncell + cidx(p, sx, y, sz));
+}
+
+// --------------------------------------------------------------------------
+// Local collision in deviation form.
+//   rho = 1 + sum g, rho u = sum g c + F/2 (Eqs. 4-5)
+//   g^eq = w (drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u))
+//   BGK: g* = g - omega (g - g^eq) + (1 - omega/2) F_i
+//   regularized: g* = g^eq + (1 - omega) P(g - g^eq) + (1 - omega/2) F_i with
+//   P the Hermite projection up to second order.
+//   F_i = w [3 (c - u).F + 9 (c.u)(c.F)] (Guo).
+// The relaxation is written with delta = 2 - omega = 4 eps / (1 + 2 eps),
+// eps = tau - 1/2 = nu_eff / c_s^2 (Eq. 8): at the paper's resolutions
+// eps ~ 1e-5, and forming omega itself in FP32 would keep only ~0.2 % of
+// the viscous part.  With delta the "-1" of (1 - omega) is applied exactly:
+//   BGK: g* = 2 g^eq - g + delta (g - g^eq); regularized: g^eq - P + delta P;
+//   force prefactor 1 - omega/2 = delta / 2.
+// --------------------------------------------------------------------------
+template <class R> __device__ __forceinline__ R relax_delta(R eps) {
+  return (R)4 * eps / ((R)1 + (R)2 * eps);
+}
+
+template <int Q, class R>
+__device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* u_out) {
+  using L = Lat<Q>;
+  R drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    drho += g[i];
+    if (L::c(i, 0)) jx += L::c(i, 0) > 0 ? g[i] : -g[i];
+    if (L::c(i, 1)) jy += L::c(i, 1) > 0 ? g[i] : -g[i];
+    if (L::c(i, 2)) jz += L::c(i, 2) > 0 ? g[i] : -g[i];
+  }
+  const R Fx = (R)p.F[0], Fy = (R)p.F[1], Fz = (R)p.F[2];
+  jx += (R)0.5 * Fx;
+  jy += (R)0.5 * Fy;
+  jz += (R)0.5 * Fz;
+  const R rho = (R)1 + drho;
+  const R inv = (R)1 / rho;
+  const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
+  u_out[0] = ux;
+  u_out[1] = uy;
+  u_out[2] = uz;
+  const R uu15 = (R)1.5 * (ux * ux + uy * uy + uz * uz);
+  const R uF = ux * Fx + uy * Fy + uz * Fz;
+  const R fpre = (R)0.5 * delta;
+  R geq[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R cu = (R)L::c(i, 0) * ux + (R)L::c(i, 1) * uy + (R)L::c(i, 2) * uz;
+    geq[i] = (R)L::w(i) * (drho + rho * ((R)3 * cu + (R)4.5 * cu * cu - uu15));
+  }
+  if (p.collision == 0) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = ((R)2 * geq[i] - g[i]) + delta * (g[i] - geq[i]);
+  } else {
+    R a[3] = {0, 0, 0}, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R n = g[i] - geq[i];
+      const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+      a[0] += (R)cx * n;
+      a[1] += (R)cy * n;
+      a[2] += (R)cz * n;
+      pxx += (R)(cx * cx) * n;
+      pyy += (R)(cy * cy) * n;
+      pzz += (R)(cz * cz) * n;
+      pxy += (R)(cx * cy) * n;
+      pxz += (R)(cx * cz) * n;
+      pyz += (R)(cy * cz) * n;
+    }
+    const R tr = (pxx + pyy + pzz) * ((R)1 / (R)3);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+      const R qp = (R)(cx * cx) * pxx + (R)(cy * cy) * pyy + (R)(cz * cz) * pzz +
+                   (R)2 * ((R)(cx * cy) * pxy + (R)(cx * cz) * pxz + (R)(cy * cz) * pyz) - tr;
+      const R ca = (R)cx * a[0] + (R)cy * a[1] + (R)cz * a[2];
+      const R P = (R)L::w(i) * ((R)3 * ca + (R)4.5 * qp);
+      g[i] = (geq[i] - P) + delta * P;
+    }
+  }
+  if (p.has_force) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+      const R cF = (R)cx * Fx + (R)cy * Fy + (R)cz * Fz;
+      const R cu = (R)cx * ux + (R)cy * uy + (R)cz * uz;
+      g[i] += fpre * (R)L::w(i) * ((R)3 * (cF - uF) + (R)9 * cu * cF);
+    }
+  }
+}
+
+}  // namespace lbm

@@ -1,0 +1,395 @@
+// lbm_kernels.cuh -- the kernels of one LBM-RANS step and their helpers.
+//
+// Per step (buffers src -> dst):
+//   k_wall  : wall pre-pass over the compacted wall-node list of each y face
+//             (slip-velocity bounce-back: Newton for u_tau, Eq. 35 slip
+//             velocity and rho_w; HRFD: rho_F, u_F after streaming (Eqs.
+//             20-22), Newton, u_B, rho_B (Eq. 23), the Eq. 27-28 gradient and
+//             the Eq. 19/26 populations), Dirichlet nu_tilde_B = nu kappa y_B+.
+//   k_bulk  : every cell: SA update (Eq. 11), pull streaming (Eq. 3) with the
+//             face rules, Zou-He inlet, HRFD populations at wall nodes,
+//             moments (Eqs. 4-5), omega from nu + nu_t (Eq. 8), collision.
+#pragma once
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// ----------------------------------------------------------------------------
+// Bulk: one thread per cell, x fastest within a warp.
+// ----------------------------------------------------------------------------
+template <int Q, int ST>
+__global__ void __launch_bounds__(256) k_bulk(const Params p) {
+  using L = Lat<Q>;
+  using C = Codec<ST>;
+  using R = typename Compute<ST>::R;
+  using T = typename C::T;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= p.nx || y >= p.ny) return;
+  const long long id = cidx(p, x, y, z);
+  const T* __restrict__ fs = (const T*)p.f_src;
+  T* __restrict__ fd = (T*)p.f_dst;
+  const R* __restrict__ us = (const R*)p.u_src;
+  R* __restrict__ ud = (R*)p.u_dst;
+  const R* __restrict__ ns = (const R*)p.nt_src;
+  R* __restrict__ nd = (R*)p.nt_dst;
+
+  int wf = -1;
+  if (y == 0 && p.wall[0] && x >= p.xw0[0]) wf = 0;
+  else if (y == p.ny - 1 && p.wall[1] && x >= p.xw0[1]) wf = 1;
+  const bool inlet = (x == 0 && p.kind[XMIN] == BC_INLET);
+
+  // 1. SA working variable of the new step (Dirichlet at wall nodes and inlet)
+  R ntn;
+  if (p.turbulent) {
+    if (wf >= 0) {
+      ntn = nd[id];
+    } else {
+      ntn = inlet ? (R)p.nt_face[XMIN] : sa_update<R, (Q == 19)>(p, ns, us, x, y, z);
+      nd[id] = ntn;
+    }
+  } else {
+    ntn = ns[id];
+    nd[id] = ntn;
+  }
+  const R nu = (R)p.nu;
+  const R nut = p.turbulent ? sa_nut<R>(ntn, nu) : (R)0;
+  const R delta = relax_delta<R>((R)3 * (nu + nut));   // 2 - omega (Eq. 8)
+
+  // 2. post-stream populations
+  R g[Q];
+  if (wf >= 0 && p.wall[wf] == BC_WALL_HRFD) {
+    const int node = z * (p.nx - p.xw0[wf]) + (x - p.xw0[wf]);
+    const R* fr = (const R*)p.frec[wf] + (long long)node * Q;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = fr[i];
+  } else if (x >= 1 && x <= p.nx - 2 && y >= 1 && y <= p.ny - 2) {
+    const int zm = z == 0 ? p.nz - 1 : z - 1;
+    const int zp = z == p.nz - 1 ? 0 : z + 1;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cz = L::c(i, 2);
+      const int sz = cz == 0 ? z : (cz > 0 ? zm : zp);
+      g[i] = (R)C::ld(fs + i * p.ncell + cidx(p, x - L::c(i, 0), y - L::c(i, 1), sz));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      bool known;
+      g[i] = pull_bc<Q, ST>(p, x, y, z, i, &known);
+    }
+    if (inlet) {
+      // Zou-He velocity inlet: unknowns c_x > 0 from the non-equilibrium
+      // bounce-back of the normal direction plus transverse corrections.
+      const R ux = (R)p.u_face[XMIN][0], uy = (R)p.u_face[XMIN][1], uz = (R)p.u_face[XMIN][2];
+      R s0 = 0, sm = 0, ky = 0, kz = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (L::c(i, 0) == 0) {
+          s0 += g[i];
+          ky += (R)L::c(i, 1) * g[i];
+          kz += (R)L::c(i, 2) * g[i];
+        } else if (L::c(i, 0) < 0) {
+          sm += g[i];
+        }
+      }
+      const R rho = ((R)1 + s0 + (R)2 * sm) / ((R)1 - ux);
+      const R Ny = (R)0.5 * ky - rho * uy / (R)3;
+      const R Nz = (R)0.5 * kz - rho * uz / (R)3;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (L::c(i, 0) > 0) {
+          const R cu = (R)L::c(i, 0) * ux + (R)L::c(i, 1) * uy + (R)L::c(i, 2) * uz;
+          g[i] = g[opp(i)] + (R)6 * (R)L::w(i) * rho * cu - (R)L::c(i, 1) * Ny - (R)L::c(i, 2) * Nz;
+        }
+      }
+    }
+  }
+
+  // 3. moments and collision
+  R u[3];
+  collide<Q, R>(p, g, delta, u);
+
+  // 4. store
+#pragma unroll
+  for (int i = 0; i < Q; ++i) C::st(fd + i * p.ncell + id, g[i]);
+  ud[id] = u[0];
+  ud[id + p.ncell] = u[1];
+  ud[id + 2 * p.ncell] = u[2];
+}
+
+// ----------------------------------------------------------------------------
+// Wall pre-pass: one thread per wall node; blockIdx.y selects the y face.
+// ----------------------------------------------------------------------------
+template <int Q, int ST>
+__global__ void __launch_bounds__(128) k_wall(const Params p) {
+  using L = Lat<Q>;
+  using C = Codec<ST>;
+  using R = typename Compute<ST>::R;
+  using T = typename C::T;
+  const int fi = blockIdx.y;
+  if (!p.wall[fi]) return;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= p.nwall[fi]) return;
+  const int nwx = p.nx - p.xw0[fi];
+  const int z = node / nwx;
+  const int x = p.xw0[fi] + node % nwx;
+  const int yB = fi == 0 ? 0 : p.ny - 1;
+  const int s = fi == 0 ? 1 : -1;   // inward direction along y
+  const R* __restrict__ us = (const R*)p.u_src;
+  const R* __restrict__ ns = (const R*)p.nt_src;
+  R* __restrict__ nd = (R*)p.nt_dst;
+  const T* __restrict__ fs = (const T*)p.f_src;
+  const double nu = p.nu;
+  const long long idB = cidx(p, x, yB, z);
+  double ut = 0.0;
+  bool ok = true;
+
+  if (p.wall[fi] == BC_WALL_BB) {
+    // Section 3.2: u_tau from the tangential velocity at the reference node
+    const int yR = yB + s * (p.ref_node[fi] - 1);
+    const double yref = (double)p.ref_node[fi] - 0.5;
+    const long long idR = cidx(p, x, yR, z);
+    const double Ux = (double)us[idR], Uz = (double)us[idR + 2 * p.ncell];
+    const double U = sqrt(Ux * Ux + Uz * Uz);
+    const double tx = U > 0.0 ? Ux / U : 1.0, tz = U > 0.0 ? Uz / U : 0.0;
+    R* uw = (R*)p.uw[fi] + 3 * node;
+    if (p.turbulent) {
+      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, U, yref, nu, p.utau[fi][node], &ut);
+      const double ypB = ut * 0.5 / nu;
+      const double nutB = nu * WF::kappa * ypB;
+      // Eq. 35 with Delta_w = 1/2 and nu_t|_B = nu kappa y_B+
+      const double slip = ut * ut * 0.5 / (nu + nutB);
+      uw[0] = (R)((double)us[idB] - slip * tx);
+      uw[1] = (R)0;
+      uw[2] = (R)((double)us[idB + 2 * p.ncell] - slip * tz);
+      nd[idB] = (R)(nu * WF::kappa * ypB);
+    } else {
+      uw[0] = uw[1] = uw[2] = (R)0;
+    }
+    R rho = (R)1;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) rho += (R)C::ld(fs + i * p.ncell + idB);
+    ((R*)p.rhow[fi])[node] = rho;
+  } else {
+    // Section 3.1: regularized node with the HRFD gradient
+    const int yF = yB + s, yFF = yB + 2 * s;
+    R jF[3] = {(R)0.5 * (R)p.F[0], (R)0.5 * (R)p.F[1], (R)0.5 * (R)p.F[2]};
+    R rhoF = (R)1;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      bool known;
+      const R gi = pull_bc<Q, ST>(p, x, yF, z, i, &known);
+      rhoF += gi;
+      jF[0] += (R)L::c(i, 0) * gi;
+      jF[1] += (R)L::c(i, 1) * gi;
+      jF[2] += (R)L::c(i, 2) * gi;
+    }
+    const double Ux = (double)(jF[0] / rhoF), Uz = (double)(jF[2] / rhoF);
+    const double U = sqrt(Ux * Ux + Uz * Uz);
+    const double tx = U > 0.0 ? Ux / U : 1.0, tz = U > 0.0 ? Uz / U : 0.0;
+    if (p.turbulent)
+      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, U, 1.5, nu, p.utau[fi][node], &ut);
+    const double ypB = ut * 0.5 / nu;
+    const double upB = p.turbulent ? ut * wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB) : 0.0;
+    const R uB[3] = {(R)(upB * tx), (R)0, (R)(upB * tz)};
+    // Eq. 23 with u_B . n = 0: rho_B = f_par + 2 f_perp (deviations: weights sum to 1)
+    R gpar = 0, gperp = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cn = -s * L::c(i, 1);   // c . n with n the outward normal
+      if (cn >= 0) {
+        bool known;
+        const R gi = pull_bc<Q, ST>(p, x, yB, z, i, &known);
+        if (cn == 0) gpar += gi; else gperp += gi;
+      }
+    }
+    const R rhoB = (R)1 + gpar + (R)2 * gperp;
+    // velocity gradient G[a][c] = d_a u_c at B from the previous-step velocity
+    R G[3][3];
+    const Nb<R> xm = neighbour<R>(p, ns, us, x, yB, z, 0, -1);
+    const Nb<R> xp = neighbour<R>(p, ns, us, x, yB, z, 0, +1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) G[0][c] = (R)0.5 * (xp.u[c] - xm.u[c]);
+    if (Q == 19) {
+      const Nb<R> zm = neighbour<R>(p, ns, us, x, yB, z, 2, -1);
+      const Nb<R> zp = neighbour<R>(p, ns, us, x, yB, z, 2, +1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) G[2][c] = (R)0.5 * (zp.u[c] - zm.u[c]);
+    } else {
+      G[2][0] = G[2][1] = G[2][2] = (R)0;
+    }
+    const long long idF = cidx(p, x, yF, z), idFF = cidx(p, x, yFF, z);
+    const double dup = ypB > 0.0 ? wf_dudy(p.wall_law, p.law_kappa, ypB) : 1.0;
+    const double ana = ut > 0.0 ? ut * ut / nu * dup : 0.0;   // Eq. 15
+    const double tdir[3] = {tx, 0.0, tz};
+    const R beta = (R)p.beta[fi];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R fd = (R)0.5 * ((R)-3 * us[idB + c * p.ncell] + (R)4 * us[idF + c * p.ncell] -
+                             us[idFF + c * p.ncell]);                       // Eq. 28
+      R dn = fd;
+      if (c != 1 && p.turbulent) dn = beta * (R)(ana * tdir[c]) + ((R)1 - beta) * fd;  // Eq. 27
+      G[1][c] = (R)s * dn;
+    }
+    const R ntB = ns[idB];
+    const R nutB = p.turbulent ? sa_nut<R>(ntB, (R)nu) : (R)0;
+    const R tau = (R)0.5 + (R)3 * ((R)nu + nutB);
+    const R Sxx = G[0][0], Syy = G[1][1], Szz = G[2][2];
+    const R Sxy = (R)0.5 * (G[0][1] + G[1][0]), Sxz = (R)0.5 * (G[0][2] + G[2][0]),
+            Syz = (R)0.5 * (G[1][2] + G[2][1]);
+    const R trS = (Sxx + Syy + Szz) / (R)3;
+    const R uu15 = (R)1.5 * (uB[0] * uB[0] + uB[2] * uB[2]);
+    R* fr = (R*)p.frec[fi] + (long long)node * Q;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+      const R cu = (R)cx * uB[0] + (R)cz * uB[2];
+      const R geq = (R)L::w(i) * ((rhoB - (R)1) + rhoB * ((R)3 * cu + (R)4.5 * cu * cu - uu15));
+      const R qs = (R)(cx * cx) * Sxx + (R)(cy * cy) * Syy + (R)(cz * cz) * Szz +
+                   (R)2 * ((R)(cx * cy) * Sxy + (R)(cx * cz) * Sxz + (R)(cy * cz) * Syz) - trS;
+      fr[i] = geq - (R)3 * (R)L::w(i) * rhoB * tau * qs;     // Eqs. 19, 26
+    }
+    if (p.turbulent) nd[idB] = (R)(nu * WF::kappa * ypB);
+  }
+  p.utau[fi][node] = ut;
+  if (!ok) atomicOr(p.flags, FLAG_NEWTON);
+}
+
+// ----------------------------------------------------------------------------
+// Initial state from physical fields: f* = f^eq(rho, u), u^0 = u.
+// ----------------------------------------------------------------------------
+template <int Q, int ST>
+__global__ void k_init(const Params p, const double* rho, const double* u, const double* nt,
+                       double rho0, double ucv, double nucv) {
+  using L = Lat<Q>;
+  using C = Codec<ST>;
+  using R = typename Compute<ST>::R;
+  using T = typename C::T;
+  const long long n = (long long)p.nx * p.ny * p.nz;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(k % p.nx);
+    const int y = (int)((k / p.nx) % p.ny);
+    const int z = (int)(k / ((long long)p.nx * p.ny));
+    const long long id = cidx(p, x, y, z);
+    const R r = (R)(rho[k] / rho0);
+    const R ux = (R)(u[k] * ucv), uy = (R)(u[k + n] * ucv), uz = (R)(u[k + 2 * n] * ucv);
+    const R uu15 = (R)1.5 * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R cu = (R)L::c(i, 0) * ux + (R)L::c(i, 1) * uy + (R)L::c(i, 2) * uz;
+      const R geq = (R)L::w(i) * ((r - (R)1) + r * ((R)3 * cu + (R)4.5 * cu * cu - uu15));
+      C::st((T*)p.f_dst + i * p.ncell + id, geq);
+    }
+    R* ud = (R*)p.u_dst;
+    ud[id] = ux;
+    ud[id + p.ncell] = uy;
+    ud[id + 2 * p.ncell] = uz;
+    ((R*)p.nt_dst)[id] = (R)(nt[k] * nucv);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Physical-unit export of rho, u, nu_t, nu_tilde into dense float64 arrays.
+// ----------------------------------------------------------------------------
+template <int Q, int ST>
+__global__ void k_fields(const Params p, double* rho, double* u, double* nut, double* nt,
+                         double rho0, double vel, double visc) {
+  using C = Codec<ST>;
+  using R = typename Compute<ST>::R;
+  using T = typename C::T;
+  const long long n = (long long)p.nx * p.ny * p.nz;
+  const T* fs = (const T*)p.f_src;
+  const R* us = (const R*)p.u_src;
+  const R* ns = (const R*)p.nt_src;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(k % p.nx);
+    const int y = (int)((k / p.nx) % p.ny);
+    const int z = (int)(k / ((long long)p.nx * p.ny));
+    const long long id = cidx(p, x, y, z);
+    double r = 1.0;
+    bool fin = true;
+    for (int i = 0; i < Q; ++i) {
+      const double gi = (double)C::ld(fs + i * p.ncell + id);
+      fin = fin && isfinite(gi);
+      r += gi;
+    }
+    if (rho) rho[k] = r * rho0;
+    if (u) {
+      u[k] = (double)us[id] * vel;
+      u[k + n] = (double)us[id + p.ncell] * vel;
+      u[k + 2 * n] = (double)us[id + 2 * p.ncell] * vel;
+    }
+    const double ntl = (double)ns[id];
+    if (nt) nt[k] = ntl * visc;
+    if (nut) {
+      const double chi = ntl / p.nu, c3 = chi * chi * chi;
+      nut[k] = p.turbulent ? ntl * c3 / (c3 + 7.1 * 7.1 * 7.1) * visc : 0.0;
+    }
+    fin = fin && isfinite((double)us[id]) && isfinite(ntl);
+    if (!fin) atomicOr(p.flags, FLAG_NONFINITE);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Deterministic FP64 reduction of mass and momentum.  Block b sums the cells
+// [b*chunk, (b+1)*chunk) with a fixed thread stride and a fixed tree; the
+// partials are summed in block order by k_reduce_final.
+// ----------------------------------------------------------------------------
+template <int Q, int ST>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(const Params p, double* partial,
+                                                        long long chunk) {
+  using L = Lat<Q>;
+  using C = Codec<ST>;
+  using T = typename C::T;
+  __shared__ double sh[RED_VALS][RED_THREADS];
+  const long long n = (long long)p.nx * p.ny * p.nz;
+  const long long b0 = blockIdx.x * chunk;
+  const long long b1 = b0 + chunk < n ? b0 + chunk : n;
+  const T* fs = (const T*)p.f_src;
+  double acc[RED_VALS] = {0, 0, 0, 0};
+  bool fin = true;
+  for (long long k = b0 + threadIdx.x; k < b1; k += RED_THREADS) {
+    const int x = (int)(k % p.nx);
+    const int y = (int)((k / p.nx) % p.ny);
+    const int z = (int)(k / ((long long)p.nx * p.ny));
+    const long long id = cidx(p, x, y, z);
+    double m = 1.0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double gi = (double)C::ld(fs + i * p.ncell + id);
+      fin = fin && isfinite(gi);
+      m += gi;
+      jx += L::c(i, 0) * gi;
+      jy += L::c(i, 1) * gi;
+      jz += L::c(i, 2) * gi;
+    }
+    acc[0] += m;
+    acc[1] += jx;
+    acc[2] += jy;
+    acc[3] += jz;
+  }
+  if (!fin) atomicOr(p.flags, FLAG_NONFINITE);
+#pragma unroll
+  for (int v = 0; v < RED_VALS; ++v) sh[v][threadIdx.x] = acc[v];
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int v = 0; v < RED_VALS; ++v) sh[v][threadIdx.x] += sh[v][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int v = 0; v < RED_VALS; ++v) partial[blockIdx.x * RED_VALS + v] = sh[v][0];
+  }
+}
+
+__global__ void k_reduce_final(const double* partial, int nblocks, double* out);
+__global__ void k_wall_stats(const Params p, double* prev, double* out);
+
+}  // namespace lbm

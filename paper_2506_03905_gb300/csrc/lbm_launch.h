@@ -1,0 +1,23 @@
+// lbm_launch.h -- host-side launchers of the step kernels (one set per lattice).
+#pragma once
+#include <cuda_runtime.h>
+#include "lbm_device.cuh"
+
+namespace lbm {
+#define LBM_DECLARE_LAUNCHERS(Q)                                                               \
+  void launch_bulk_q##Q(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s);              \
+  void launch_wall_q##Q(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s);              \
+  void launch_init_q##Q(int st, const Params& p, int grid, const double* rho, const double* u, \
+                        const double* nt, double rho0, double ucv, double nucv, cudaStream_t s); \
+  void launch_fields_q##Q(int st, const Params& p, int grid, double* rho, double* u,          \
+                          double* nut, double* nt, double rho0, double vel, double visc,       \
+                          cudaStream_t s);                                                     \
+  void launch_reduce_q##Q(int st, const Params& p, int blocks, double* partial,              \
+                          long long chunk, cudaStream_t s);
+LBM_DECLARE_LAUNCHERS(9)
+LBM_DECLARE_LAUNCHERS(19)
+#undef LBM_DECLARE_LAUNCHERS
+
+void launch_reduce_final(const double* partial, int nblocks, double* out, cudaStream_t s);
+void launch_wall_stats(const Params& p, double* prev, double* out, cudaStream_t s);
+}  // namespace lbm

@@ -1,0 +1,214 @@
+"""GPU (C ABI) versus the FP64 oracle on the same seeded inputs.
+
+Tolerance for FP32 storage: ||gpu - oracle||_inf / ||oracle||_inf <= 1e-5 per
+field (u, nu_t, wall u_tau and C_f); FP64 storage: 1e-9.  Sizes span several
+32 x 8 thread blocks with a ragged tail in x and y.
+"""
+import numpy as np
+import pytest
+
+import lbm_cases as C
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "fp32": 1e-5}
+
+
+def rel(a, b):
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def run_gpu(case, nsteps, fields=None, split=None):
+    import paper_2506_03905_gb300 as pkg
+    init = C.initial_fields(case)
+    s = pkg.Solver(case)
+    s.set_fields(*init)
+    if split:
+        for k in split:
+            s.step(k)
+    else:
+        s.step(nsteps)
+    names = ["rho", "u", "nu_t", "nu_tilde"]
+    for f in ("ymin", "ymax"):
+        if case.bcs[f].kind in ("wall_bb", "wall_hrfd"):
+            names += ["u_tau_" + f, "cf_" + f]
+    out = s.fields(names)
+    s.close()
+    return out
+
+
+def run_oracle(case, nsteps):
+    return Oracle(case, *C.initial_fields(case)).run(nsteps).fields()
+
+
+def compare(case, nsteps, tol, keys=None):
+    g = run_gpu(case, nsteps)
+    r = run_oracle(case, nsteps)
+    keys = keys or [k for k in g if k in r]
+    errs = {k: rel(g[k], r[k]) for k in keys}
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, (case.name, errs)
+    return errs
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_half_channel_2d_log_law(storage):
+    """2-D half channel of the first workload (D2Q9, BGK, SA, log-law
+    bounce-back at the first node, symmetry centreline) from rest."""
+    case = C.half_channel_2d(storage=storage).replace(u_init=(0.3, 0.0, 0.0))
+    compare(case, 400, TOL[storage])
+
+
+@pytest.mark.parametrize("scheme", ["wall_bb", "wall_hrfd"])
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_channel_3d(scheme, storage):
+    case = C.channel_3d(re_tau=5200.0, scheme=scheme, nx=40, ny=20, nz=5, seed=2,
+                        storage=storage)
+    compare(case, 120, TOL[storage])
+
+
+@pytest.mark.parametrize("scheme", ["wall_bb", "wall_hrfd"])
+def test_channel_3d_regularized_ref_b(scheme):
+    ref = 1 if scheme == "wall_bb" else 2
+    case = C.channel_3d(re_tau=1000.0, scheme=scheme, nx=36, ny=18, nz=3, seed=4,
+                        collision="regularized", ref_node=ref)
+    compare(case, 100, TOL["fp32"])
+
+
+@pytest.mark.parametrize("scheme", ["wall_bb", "wall_hrfd"])
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_flat_plate(scheme, lattice):
+    nz = 1 if lattice == "D2Q9" else 3
+    case = C.flat_plate_3d(nx=70, ny=22, nz=nz, dx=3e-2, scheme=scheme).replace(lattice=lattice)
+    compare(case, 150, TOL["fp32"])
+
+
+def test_flat_plate_symmetry_top():
+    case = C.flat_plate_3d(nx=50, ny=12, nz=2, dx=4e-2, scheme="wall_bb", top="symmetry")
+    compare(case, 100, TOL["fp32"])
+
+
+def test_laminar_poiseuille_closed_form_on_gpu():
+    """SA off, half-way bounce-back on both walls: the steady GPU profile is the
+    half-way bounce-back parabola with its tau-dependent slip (see the oracle pin).
+    The viscosity is chosen so that tau0 = 0.8 (a few thousand steps to steady)."""
+    import paper_2506_03905_gb300 as pkg
+    ny = 8
+    base = C.half_channel_2d(ny=ny, nx=1, storage="fp64")
+    dt = base.mach * base.dx / (3.0 ** 0.5 * base.u_ref)
+    nu = 0.1 * base.dx ** 2 / dt                     # lattice viscosity 0.1
+    case = base.replace(turbulence="laminar", nu=nu, bcs={"ymax": C.BC("wall_bb")})
+    s = pkg.Solver(case)
+    s.set_fields(*C.initial_fields(case))
+    lp = s.lattice_params()
+    assert lp["tau0"] == pytest.approx(0.8, rel=1e-12)
+    nsteps = int(60 * ny * ny / (3.0 * lp["nu"])) + 200
+    assert nsteps < 20000
+    s.step(nsteps)
+    u = s.fields(["u"])["u"][0, 0, :, 0] * lp["dt"] / case.dx
+    s.close()
+    tau, g, nu_lb = lp["tau0"], lp["F"][0], lp["nu"]
+    y = np.arange(ny) + 0.5
+    ua = g / (2 * nu_lb) * y * (ny - y) + g / nu_lb * (2.0 / 3.0 * (tau - 0.5) ** 2 - 0.125)
+    assert rel(u, ua) < 1e-6
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("scheme", ["wall_bb", "wall_hrfd"])
+def test_rest_state_bit_exact(storage, scheme):
+    """rho = 1, u = 0, F = 0: the shifted deviations stay exactly zero."""
+    case = C.channel_3d(scheme=scheme, nx=33, ny=12, nz=3, storage=storage).replace(
+        force=(0.0, 0.0, 0.0), u_init=(0.0, 0.0, 0.0), perturb=0.0)
+    g = run_gpu(case, 25)
+    assert np.abs(g["u"]).max() == 0.0
+    assert np.all(g["rho"] == case.rho0)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp64"])
+def test_mass_conservation_fp64_sums(storage):
+    import paper_2506_03905_gb300 as pkg
+    case = C.channel_3d(scheme="wall_bb", nx=40, ny=20, nz=6, storage=storage)
+    s = pkg.Solver(case)
+    s.set_fields(*C.initial_fields(case))
+    d0 = s.diagnostics()
+    s.step(50)
+    d1 = s.diagnostics()
+    s.close()
+    tol = 1e-13 if storage == "fp64" else 2e-6
+    assert abs(d1.mass - d0.mass) / d0.mass < tol
+    assert d1.mean_u_tau[0] > 0 and d1.nonfinite == 0
+
+
+def test_checkpoint_resume_bit_exact():
+    import paper_2506_03905_gb300 as pkg
+    case = C.channel_3d(scheme="wall_hrfd", nx=24, ny=12, nz=3)
+    a = pkg.Solver(case)
+    a.set_fields(*C.initial_fields(case))
+    a.step(30)
+    ua = a.fields(["u", "nu_tilde"])
+    b = pkg.Solver(case)
+    b.set_fields(*C.initial_fields(case))
+    b.step(15)
+    st = b.get_state()
+    b.close()
+    c = pkg.Solver(case)
+    c.set_state(st)
+    c.step(15)
+    uc = c.fields(["u", "nu_tilde"])
+    a.close()
+    c.close()
+    assert np.array_equal(ua["u"], uc["u"]) and np.array_equal(ua["nu_tilde"], uc["nu_tilde"])
+
+
+def test_graph_and_single_steps_agree_bit_exact():
+    case = C.channel_3d(scheme="wall_bb", nx=24, ny=12, nz=3)
+    a = run_gpu(case, 9)
+    b = run_gpu(case, 9, split=[1, 1, 3, 4])
+    assert np.array_equal(a["u"], b["u"])
+
+
+@pytest.mark.parametrize("nx,ny,nz,lattice", [(1, 6, 1, "D2Q9"), (3, 3, 1, "D2Q9"),
+                                              (5, 6, 1, "D3Q19"), (2, 7, 2, "D3Q19")])
+def test_degenerate_sizes(nx, ny, nz, lattice):
+    case = C.channel_3d(scheme="wall_bb", nx=nx, ny=ny, nz=nz).replace(lattice=lattice)
+    compare(case, 40, TOL["fp32"])
+
+
+def test_zero_steps_is_identity():
+    case = C.channel_3d(scheme="wall_bb", nx=8, ny=6, nz=2)
+    g = run_gpu(case, 0)
+    rho, u, nut = C.initial_fields(case)
+    assert rel(g["u"], u) < 1e-7 and rel(g["rho"], rho) < 1e-7
+
+
+def test_invalid_boundary_combinations():
+    import paper_2506_03905_gb300 as pkg
+    case = C.channel_3d(nx=8, ny=6, nz=2)
+    s = pkg.Solver(case)
+    for face, kind in [(0, "wall_bb"), (2, "inlet_zouhe"), (4, "symmetry"), (1, "inlet_zouhe")]:
+        with pytest.raises(pkg.LbmError):
+            pkg.lbm_set_bc(s.ctx, face, pkg.bc_struct(C.BC(kind)))
+    with pytest.raises(pkg.LbmError):
+        pkg.lbm_set_bc(s.ctx, 2, pkg.bc_struct(C.BC("wall_hrfd", ref_node=1)))
+    # unpaired periodic face is caught when the state is set
+    pkg.lbm_set_bc(s.ctx, 3, pkg.bc_struct(C.BC("periodic")))
+    pkg.lbm_set_bc(s.ctx, 2, pkg.bc_struct(C.BC("wall_bb")))
+    with pytest.raises(pkg.LbmError):
+        s.set_fields(*C.initial_fields(case))
+    s.close()
+
+
+def test_nonfinite_is_reported():
+    import paper_2506_03905_gb300 as pkg
+    case = C.channel_3d(scheme="wall_bb", nx=8, ny=6, nz=2)
+    rho, u, nut = C.initial_fields(case)
+    u[0, 1, 2, 3] = np.nan
+    s = pkg.Solver(case)
+    s.set_fields(rho, u, nut)
+    s.step(2)
+    s.fields(["u"], check=False)
+    assert s.last_status == pkg.LBM_ENONFINITE
+    assert s.diagnostics().nonfinite == 1
+    s.close()
