@@ -176,6 +176,25 @@ const char* lbm_last_error(const lbm_ctx* ctx);
    (lattice), out[2] = tau0, out[3..5] = F (lattice). */
 lbm_status lbm_lattice_params(const lbm_ctx* ctx, double out[6]);
 
+/* Mass and momentum (lattice units: out[0] = sum of populations, out[1..3] =
+   sum of c_i f_i) of a caller-owned population array, computed without
+   allocating any memory.  The paper has no counterpart: this serves callers
+   that cannot allocate device memory at the point of the call (applications
+   that hand the library fixed buffers, allocators that forbid growth, loops
+   where an allocation would synchronise the device).
+   f: device pointer to Q * pitch*ny*nz populations in `storage` precision,
+      laid out as lbm_get_state's population block (shifted deviations
+      f_i - w_i, x fastest, rows of `pitch` >= nx elements).
+   out: device pointer to 4 doubles, written asynchronously on `stream`.
+   Partial sums live in one fixed 128 KiB static device array shared by all
+   calls (held on every GPU that loads the library until exit): lattices above
+   16,777,216 cells are rejected with LBM_EINVAL, calls that overlap on the GPU
+   race and must be serialised by the caller, and the first call on each device
+   looks up the array's address (make it before any stream capture).  Errors
+   are described by lbm_last_error(NULL). */
+lbm_status lbm_moments_noalloc(const void* f, int lattice, int storage, int nx, int ny, int nz,
+                               int pitch, double* out, void* stream);
+
 /* ------------------------------------------------------------------------
  * Batched sweeps: many independent contexts advanced together by one
  * persistent, cooperative kernel launch per lbm_batch_step call (captured in

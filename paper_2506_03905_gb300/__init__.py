@@ -25,7 +25,7 @@ __all__ = [
     "lbm_create", "lbm_set_bc", "lbm_set_fields", "lbm_step", "lbm_step_timed", "lbm_fields",
     "lbm_diagnostics", "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_destroy",
     "lbm_last_error", "lbm_lattice_params", "lbm_batch_create", "lbm_batch_step",
-    "lbm_batch_tune", "lbm_batch_destroy", "lbm_batch_last_error",
+    "lbm_batch_tune", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_moments_noalloc",
 ]
 
 LIB_PATH = _build.LIB
@@ -119,6 +119,8 @@ def lib():
         "lbm_batch_tune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
         "lbm_batch_destroy": (None, [_P]),
         "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
+        "lbm_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -228,6 +230,12 @@ def lbm_batch_tune(b):
 
 def lbm_batch_destroy(b):
     lib().lbm_batch_destroy(b)
+
+
+def lbm_moments_noalloc(f_ptr, lattice: int, storage: int, nx: int, ny: int, nz: int,
+                        pitch: int, out_ptr, stream=0) -> int:
+    """Raw status of the allocation-free mass/momentum reduction (see include/lbm.h)."""
+    return lib().lbm_moments_noalloc(f_ptr, lattice, storage, nx, ny, nz, pitch, out_ptr, stream)
 
 
 def lbm_batch_last_error(b=None) -> str:
