@@ -93,6 +93,9 @@ typedef struct {
   int turbulence;              /* LBM_SA | LBM_LAMINAR */
   int wall_law;                /* LBM_LAW_SA_ANALYTIC (Eq. 16) | LBM_LAW_LOG */
   double kappa, B;             /* log-law constants */
+  double u_shift;              /* m/s, x velocity U of the stored deviations: populations are
+                                  kept as f_i - f_i^eq(rho0, U x) (0: f_i - w_i rho0); set it
+                                  to the mean flow to keep the stored values small */
   void* (*alloc)(size_t bytes, void* user);  /* optional device allocator */
   void (*free)(void* ptr, void* user);
   void* alloc_user;
@@ -184,7 +187,9 @@ lbm_status lbm_lattice_params(const lbm_ctx* ctx, double out[6]);
    where an allocation would synchronise the device).
    f: device pointer to Q * pitch*ny*nz populations in `storage` precision,
       laid out as lbm_get_state's population block (shifted deviations
-      f_i - w_i, x fastest, rows of `pitch` >= nx elements).
+      f_i - w_i, x fastest, rows of `pitch` >= nx elements).  For a state
+      created with a nonzero u_shift the block holds f_i - f_i^eq(rho0, U x)
+      and out[1] then lacks the constant U (lattice units) per cell.
    out: device pointer to 4 doubles, written asynchronously on `stream`.
    Partial sums live in one fixed 128 KiB static device array shared by all
    calls (held on every GPU that loads the library until exit): lattices above

@@ -82,6 +82,7 @@ class Case:
     seed: int = 0
     nut_ratio_init: float = 3.0       # initial nu_tilde / nu
     steps: int = 100
+    u_shift: Optional[float] = None   # storage reference velocity (None: u_init x)
 
     def __post_init__(self):
         if self.lattice not in ("D2Q9", "D3Q19"):

@@ -58,7 +58,7 @@ class LbmConfig(ctypes.Structure):
         ("force", ctypes.c_double * 3), ("origin", ctypes.c_double * 3),
         ("collision", ctypes.c_int), ("storage", ctypes.c_int), ("turbulence", ctypes.c_int),
         ("wall_law", ctypes.c_int), ("kappa", ctypes.c_double), ("B", ctypes.c_double),
-        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+        ("u_shift", ctypes.c_double), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -256,6 +256,9 @@ def config_from_case(case, stream=0) -> LbmConfig:
     c.turbulence = TURBULENCE[case.turbulence]
     c.wall_law = WALL_LAW[case.wall_law]
     c.kappa, c.B = case.kappa, case.B
+    # stored populations are deviations from the equilibrium at the mean flow
+    shift = getattr(case, "u_shift", None)
+    c.u_shift = case.u_init[0] if shift is None else shift
     c.stream = stream
     return c
 

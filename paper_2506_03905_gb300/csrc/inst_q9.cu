@@ -4,13 +4,39 @@
 
 namespace lbm {
 
+// Launch with an explicit priority attribute (prio != 0), which a captured
+// graph kernel node keeps; the wall branch of a step uses the highest priority
+// so that it runs beside the inner-row grid instead of after it.
+template <typename... A>
+static void launch_prio(void (*k)(A...), dim3 g, dim3 b, cudaStream_t s, int prio, A... args) {
+  if (prio == 0) {
+    k<<<g, b, 0, s>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = prio;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <int ST>
-static void bulk_st(const Params& p, dim3 g, dim3 b, cudaStream_t s) {
-  k_bulk<9, ST><<<g, b, 0, s>>>(p);
+static void bulk_st(const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, int prio) {
+  // the face logic is needed unless every cell of the launch has periodic or
+  // in-lattice neighbours: periodic x and either periodic y or inner rows only
+  const bool fast = p.px && (p.py || rows == ROWS_INNER);
+  if (fast) launch_prio(k_bulk<9, ST, false>, g, b, s, prio, p, rows);
+  else launch_prio(k_bulk<9, ST, true>, g, b, s, prio, p, rows);
 }
 template <int ST>
-static void wall_st(const Params& p, dim3 g, dim3 b, cudaStream_t s) {
-  k_wall<9, ST><<<g, b, 0, s>>>(p);
+static void wall_st(const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
+  launch_prio(k_wall<9, ST>, g, b, s, prio, p);
 }
 
 #define LBM_DISPATCH(FN, ...)                       \
@@ -21,11 +47,11 @@ static void wall_st(const Params& p, dim3 g, dim3 b, cudaStream_t s) {
     default: FN<ST_FP64>(__VA_ARGS__); break;       \
   }
 
-void launch_bulk_q9(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s) {
-  LBM_DISPATCH(bulk_st, p, g, b, s)
+void launch_bulk_q9(int st, const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, int prio) {
+  LBM_DISPATCH(bulk_st, p, rows, g, b, s, prio)
 }
-void launch_wall_q9(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s) {
-  LBM_DISPATCH(wall_st, p, g, b, s)
+void launch_wall_q9(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
+  LBM_DISPATCH(wall_st, p, g, b, s, prio)
 }
 
 template <int ST>

@@ -20,6 +20,9 @@ struct lbm_ctx {
   double F_lb[3] = {0, 0, 0};
   cudaStream_t stream = nullptr;   // caller's stream
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side_stream = nullptr;  // wall pre-pass branch of a step
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int prio_hi = 0;                     // greatest stream priority of the device
   void* f[2] = {nullptr, nullptr};
   void* u[2] = {nullptr, nullptr};
   void* nt[2] = {nullptr, nullptr};
@@ -50,4 +53,4 @@ struct lbm_ctx {
 void lbm_ctx_set_error(lbm_ctx* c, const char* fmt, ...);
 lbm_status lbm_ctx_finalize(lbm_ctx* c);
 lbm::Params lbm_ctx_params(const lbm_ctx* c, int src);
-void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, dim3* g, dim3* b);
+void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b);

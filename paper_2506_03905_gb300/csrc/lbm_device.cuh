@@ -1,8 +1,11 @@
 // lbm_device.cuh -- device-side building blocks of the LBM-RANS step.
 //
 // Lattice units throughout (dx = dt = 1, c_s^2 = 1/3).  Populations are stored
-// as shifted deviations g_i = f_i - w_i (rho0 = 1) in the storage type, and all
-// arithmetic runs in the compute type R (float, or double for the FP64 mode).
+// as deviations h_i = f_i - E_i from the equilibrium at rest density and a
+// constant reference velocity U along x, E_i = f_i^eq(1, U x) (U = 0 gives
+// h_i = f_i - w_i).  All arithmetic runs on these small deviations in the
+// compute type R (float, or double for the FP64 mode): a force or viscous
+// increment per step is then many ulps of the stored value instead of a few.
 //
 // Memory layout (structure of arrays, x fastest, rows padded to `pitch`):
 //   f[q][z][y][x]  -> f[q * ncell + (z*ny + y)*pitch + x]
@@ -23,6 +26,9 @@ enum BcKind {
 enum { XMIN = 0, XMAX = 1, YMIN = 2, YMAX = 3 };
 enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2, ST_FP64 = 3 };
 enum { FLAG_NONFINITE = 1u, FLAG_NEWTON = 2u };
+// k_bulk row sets: ROWS_ALL every row; ROWS_INNER rows 1..ny-2 (independent of
+// the wall pre-pass, so they run concurrently with it); ROWS_WALL rows 0, ny-1.
+enum { ROWS_ALL = 0, ROWS_INNER = 1, ROWS_WALL = 2 };
 constexpr int RED_THREADS = 256;   // FP64 reduction block size
 constexpr int RED_VALS = 4;        // mass, momentum x/y/z
 
@@ -98,6 +104,13 @@ template <> struct Codec<ST_BF16> {
 template <int ST> struct Compute { using R = float; };
 template <> struct Compute<ST_FP64> { using R = double; };
 
+// Arithmetic helpers: FP32 uses the fast hardware reciprocal-based divide and
+// power (a few ulp, far below the 1e-5 parity tolerance); FP64 stays exact.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float pow_sixth(float x) { return __powf(x, 1.0f / 6.0f); }
+__device__ __forceinline__ double pow_sixth(double x) { return pow(x, 1.0 / 6.0); }
+
 // --------------------------------------------------------------------------
 // Kernel parameters (lattice units), passed by value.
 // --------------------------------------------------------------------------
@@ -110,6 +123,11 @@ struct Params {
   int has_force;
   double nu;                   // molecular viscosity (lattice)
   double F[3];                 // body force density (lattice)
+  double guoA[19];             // 3 w_i c_i.F per direction (Guo forcing coefficient)
+  double Ush;                  // reference velocity U (x) of the stored deviations
+  // float copies for the FP32 kernels: converting a double per thread would run
+  // on the FP64 pipe, which on GB300 has 1/64 of the FP32 rate
+  float nu_f, F_f[3], guoA_f[19], Ush_f, xs_lb_f[2], u_face_f[4][3], nt_face_f[4];
   double law_kappa, law_B;
   int kind[6];                 // face kinds
   int px, py;                  // x / y periodic
@@ -136,6 +154,11 @@ struct Params {
   unsigned* flags;
 };
 
+// Parameter in the compute type: the float copy for FP32, the double for FP64.
+template <class R> __device__ __forceinline__ R psel(double d, float f);
+template <> __device__ __forceinline__ float psel<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double psel<double>(double d, float) { return d; }
+
 __device__ __forceinline__ long long cidx(const Params& p, int x, int y, int z) {
   return ((long long)z * p.ny + y) * p.pitch + x;
 }
@@ -156,34 +179,39 @@ template <class R> __device__ __forceinline__ R sa_fv1(R chi) {
 }
 
 // nu_t = nu_tilde f_v1(nu_tilde / nu) (Eq. 10)
-template <class R> __device__ __forceinline__ R sa_nut(R nt, R nu) { return nt * sa_fv1<R>(nt / nu); }
+template <class R> __device__ __forceinline__ R sa_nut(R nt, R nu) {
+  const R chi = fdiv(nt, nu);
+  const R c3 = chi * chi * chi;
+  return nt * fdiv(c3, c3 + (R)(SAConst::cv1 * SAConst::cv1 * SAConst::cv1));
+}
 
 // P - D of Eq. 12 with S~ (Eq. 13, kept positive by the ICCFD7 limiter) and r, f_w (Eq. 14)
 template <class R> __device__ __forceinline__ R sa_source(R nt, R S, R nu, R inv_d2) {
   const R kap = (R)SAConst::kappa;
   const R cw1 = (R)SAConst::cb1 / (kap * kap) + ((R)1 + (R)SAConst::cb2) / (R)SAConst::sigma;
-  const R chi = nt / nu;
-  const R fv1 = sa_fv1<R>(chi);
-  const R fv2 = (R)1 - chi / ((R)1 + chi * fv1);
+  const R chi = fdiv(nt, nu);
+  const R c3 = chi * chi * chi;
+  const R fv1 = fdiv(c3, c3 + (R)(SAConst::cv1 * SAConst::cv1 * SAConst::cv1));
+  const R fv2 = (R)1 - fdiv(chi, (R)1 + chi * fv1);
   const R inv_kd2 = inv_d2 / (kap * kap);
   const R sbar = nt * fv2 * inv_kd2;
   R st;
   if (sbar >= -(R)SAConst::cv2lim * S) {
     st = S + sbar;
   } else {
-    st = S + S * ((R)(SAConst::cv2lim * SAConst::cv2lim) * S + (R)SAConst::cv3lim * sbar) /
-                 (((R)SAConst::cv3lim - (R)2 * (R)SAConst::cv2lim) * S - sbar);
+    st = S + fdiv(S * ((R)(SAConst::cv2lim * SAConst::cv2lim) * S + (R)SAConst::cv3lim * sbar),
+                  ((R)SAConst::cv3lim - (R)2 * (R)SAConst::cv2lim) * S - sbar);
   }
   R r = (R)SAConst::rlim;
   if (st > (R)0) {
-    const R q = nt * inv_kd2 / st;
+    const R q = fdiv(nt * inv_kd2, st);
     r = q < r ? q : r;
   }
   const R r2 = r * r, r6 = r2 * r2 * r2;
   const R g = r + (R)SAConst::cw2 * (r6 - r);
   const R g2 = g * g, g6 = g2 * g2 * g2;
   const R cw36 = (R)64;  // c_w3^6
-  const R fw = g * pow(((R)1 + cw36) / (g6 + cw36), (R)(1.0 / 6.0));
+  const R fw = g * pow_sixth(fdiv((R)1 + cw36, g6 + cw36));
   return (R)SAConst::cb1 * st * nt - cw1 * fw * nt * nt * inv_d2;
 }
 
@@ -218,10 +246,10 @@ __device__ Nb<R> neighbour(const Params& p, const R* __restrict__ nt, const R* _
     const int k = p.kind[f];
     if (k == BC_OUTLET) return load_nb<R>(p, nt, u, x, y, z);
     Nb<R> n;  // inlet (and any prescribed face)
-    n.nt = (R)p.nt_face[f];
-    n.u[0] = (R)p.u_face[f][0];
-    n.u[1] = (R)p.u_face[f][1];
-    n.u[2] = (R)p.u_face[f][2];
+    n.nt = psel<R>(p.nt_face[f], p.nt_face_f[f]);
+    n.u[0] = psel<R>(p.u_face[f][0], p.u_face_f[f][0]);
+    n.u[1] = psel<R>(p.u_face[f][1], p.u_face_f[f][1]);
+    n.u[2] = psel<R>(p.u_face[f][2], p.u_face_f[f][2]);
     return n;
   }
   if (axis == 1) {
@@ -232,10 +260,10 @@ __device__ Nb<R> neighbour(const Params& p, const R* __restrict__ nt, const R* _
     const int k = p.kind[f];
     if (k == BC_FREESTREAM) {
       Nb<R> n;
-      n.nt = (R)p.nt_face[f];
-      n.u[0] = (R)p.u_face[f][0];
-      n.u[1] = (R)p.u_face[f][1];
-      n.u[2] = (R)p.u_face[f][2];
+      n.nt = psel<R>(p.nt_face[f], p.nt_face_f[f]);
+      n.u[0] = psel<R>(p.u_face[f][0], p.u_face_f[f][0]);
+      n.u[1] = psel<R>(p.u_face[f][1], p.u_face_f[f][1]);
+      n.u[2] = psel<R>(p.u_face[f][2], p.u_face_f[f][2]);
       return n;
     }
     Nb<R> n = load_nb<R>(p, nt, u, x, y, z);  // mirror
@@ -256,14 +284,14 @@ template <class R> __device__ __forceinline__ R inv_wall_dist2(const Params& p, 
       const R dy = f == 0 ? (R)y + (R)0.5 : (R)(p.ny - y) - (R)0.5;
       R e = dy * dy;
       if (x < p.xw0[f]) {
-        const R dxl = ((R)x + (R)0.5) - (R)p.xs_lb[f];
+        const R dxl = ((R)x + (R)0.5) - psel<R>(p.xs_lb[f], p.xs_lb_f[f]);
         e += dxl * dxl;
       }
       d2 = e < d2 ? e : d2;
       any = true;
     }
   }
-  return any ? (R)1 / d2 : (R)0;
+  return any ? fdiv((R)1, d2) : (R)0;
 }
 
 // Explicit Euler update of Eq. 11 at one cell, clipped at zero.
@@ -271,7 +299,7 @@ template <class R, bool THREE_D>
 __device__ R sa_update(const Params& p, const R* __restrict__ nt, const R* __restrict__ u, int x,
                        int y, int z) {
   const Nb<R> c = load_nb<R>(p, nt, u, x, y, z);
-  const R nu = (R)p.nu;
+  const R nu = psel<R>(p.nu, p.nu_f);
   Nb<R> m[3], pl[3];
   m[0] = neighbour<R>(p, nt, u, x, y, z, 0, -1);
   pl[0] = neighbour<R>(p, nt, u, x, y, z, 0, +1);
@@ -302,8 +330,55 @@ __device__ R sa_update(const Params& p, const R* __restrict__ nt, const R* __res
   }
   const R inv_d2 = inv_wall_dist2<R>(p, x, y);
   const R rhs = -conv + sa_source<R>(c.nt, S, nu, inv_d2) +
-                (diff + (R)SAConst::cb2 * grad2) / (R)SAConst::sigma;
+                (diff + (R)SAConst::cb2 * grad2) * (R)(1.0 / SAConst::sigma);
   const R nn = c.nt + rhs;
+  return nn > (R)0 ? nn : (R)0;
+}
+
+// Same update for a cell whose six neighbours are all inside the lattice
+// (periodic z handled by the plane offsets ozm / ozp); no ghost logic.
+template <class R, bool THREE_D>
+__device__ __forceinline__ R sa_update_interior(const Params& p, const R* __restrict__ nt,
+                                                const R* __restrict__ u, int id, int nc, int oxm,
+                                                int oxp, int oym, int oyp, int ozm, int ozp, int x,
+                                                int y) {
+  const R nu = psel<R>(p.nu, p.nu_f);
+  const R h = (R)0.5;
+  const R c = nt[id];
+  R ntm[3], ntp[3];
+  ntm[0] = nt[id + oxm];
+  ntp[0] = nt[id + oxp];
+  ntm[1] = nt[id + oym];
+  ntp[1] = nt[id + oyp];
+  const R ux = u[id], uy = u[id + nc], uz = THREE_D ? u[id + 2 * nc] : (R)0;
+  // vorticity by central differences of the previous-step velocity
+  R wz = h * ((u[nc + id + oxp] - u[nc + id + oxm]) - (u[id + oyp] - u[id + oym]));
+  R S2 = wz * wz;
+  if (THREE_D) {
+    ntm[2] = nt[id + ozm];
+    ntp[2] = nt[id + ozp];
+    const R wx = h * ((u[2 * nc + id + oyp] - u[2 * nc + id + oym]) -
+                      (u[nc + id + ozp] - u[nc + id + ozm]));
+    const R wy = h * ((u[id + ozp] - u[id + ozm]) - (u[2 * nc + id + oxp] - u[2 * nc + id + oxm]));
+    S2 += wx * wx + wy * wy;
+  } else {
+    ntm[2] = c;
+    ntp[2] = c;
+  }
+  const R S = sqrt(S2);
+  const R ua[3] = {ux, uy, uz};
+  R conv = 0, diff = 0, grad2 = 0;
+#pragma unroll
+  for (int a = 0; a < (THREE_D ? 3 : 2); ++a) {
+    conv += ua[a] > (R)0 ? ua[a] * (c - ntm[a]) : ua[a] * (ntp[a] - c);
+    diff += (nu + h * (c + ntp[a])) * (ntp[a] - c) - (nu + h * (c + ntm[a])) * (c - ntm[a]);
+    const R g = h * (ntp[a] - ntm[a]);
+    grad2 += g * g;
+  }
+  const R inv_d2 = inv_wall_dist2<R>(p, x, y);
+  const R rhs = -conv + sa_source<R>(c, S, nu, inv_d2) +
+                (diff + (R)SAConst::cb2 * grad2) * (R)(1.0 / SAConst::sigma);
+  const R nn = c + rhs;
   return nn > (R)0 ? nn : (R)0;
 }
 
@@ -333,23 +408,24 @@ __host__ __device__ inline double wf_dudy(int law, double kap, double yp) {
   return (cv3 + ky3) / (cv3 + (1.0 + ky) * ky3);
 }
 
-// Solve U = u u+(u y / nu) for u >= 0.  Newton steps inside a sign-change
-// bracket, bisection when a step leaves it; stops at a relative step below
-// 1e-15.  Returns false if the iteration limit was reached.
+// Solve U = u u+(u y / nu) for u >= 0 (FP64).  Newton from the previous
+// u_tau (or sqrt(U nu / y), the viscous-sublayer value) inside a sign-change
+// bracket [lo, hi] that starts as [0, inf) and tightens with every residual;
+// a step that would leave the bracket is replaced by bisection (or doubling
+// while hi is still open).  Once a Newton step is below 1e-7 of u_tau the
+// stepped value is returned: quadratic convergence leaves an error of order
+// step^2 / u_tau (about 1e-14 relative); warm-started from the previous step's
+// u_tau this is usually a single FP64 evaluation.  Returns false if the 100-iteration limit was
+// reached (the last iterate is still returned).
 __host__ __device__ inline bool solve_utau(int law, double kap, double B, double U, double y,
                                            double nu, double guess, double* out) {
   if (!(U > 0.0)) {
     *out = 0.0;
     return true;
   }
-  double lo = 0.0, hi = fmax(U, sqrt(U * nu / y));
-  for (int k = 0; k < 400; ++k) {
-    const double yp = hi * y / nu;
-    if (hi * wf_uplus(law, kap, B, yp) - U > 0.0) break;
-    hi *= 2.0;
-  }
-  double x = (guess > lo && guess < hi) ? guess : 0.5 * (lo + hi);
-  for (int it = 0; it < 200; ++it) {
+  double lo = 0.0, hi = 0.0;  // hi == 0: not bracketed from above yet
+  double x = guess > 0.0 ? guess : sqrt(U * nu / y);
+  for (int it = 0; it < 100; ++it) {
     const double yp = x * y / nu;
     const double up = wf_uplus(law, kap, B, yp);
     const double g = x * up - U;
@@ -359,16 +435,50 @@ __host__ __device__ inline bool solve_utau(int law, double kap, double B, double
     }
     if (g < 0.0) lo = x; else hi = x;
     const double dg = up + yp * wf_dudy(law, kap, yp);
-    double xn = x - g / dg;
-    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-    if (fabs(xn - x) <= 1e-15 * fabs(xn)) {
+    const double step = g / dg;
+    double xn = x - step;
+    if (fabs(step) <= 1e-7 * x && xn > 0.0) {
+      // quadratic convergence: the error of xn is of order step^2 / x (< 1e-13 x)
       *out = xn;
       return true;
     }
+    if (!(xn > lo) || (hi > 0.0 && !(xn < hi)) || !(dg > 0.0)) xn = hi > 0.0 ? 0.5 * (lo + hi) : 2.0 * x;
     x = xn;
   }
   *out = x;
   return false;
+}
+
+// f_i^eq(rho, u) - E_i written in the small quantities drho = rho - 1 and
+// du = u - U x (u = U x + du):
+//   w [drho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u) + 3 c.du + 4.5 c.du (2 c_x U + c.du)
+//      - 1.5 du.(2 U x + du)]
+// (second-order Hermite equilibrium, Eq. 17).  uu15 = 1.5 u.u, du15 = 1.5 du.(2Ux + du).
+// With cu = c.u, cU = c_x U, cdu = c.du this is w (drho A + D),
+//   A = 1 + cu (3 + 4.5 cu) - uu15,  D = cdu (3 + 4.5 (cu + cU)) - du15.
+template <int Q, class R>
+__device__ __forceinline__ R heq_cdu(int i, R cdu, R drho, R U, R one_m_uu15, R du15) {
+  using L = Lat<Q>;
+  const R cU = L::c(i, 0) > 0 ? U : (L::c(i, 0) < 0 ? -U : (R)0);
+  const R cu = cU + cdu;
+  const R A = cu * ((R)3 + (R)4.5 * cu) + one_m_uu15;
+  const R D = cdu * ((R)3 + (R)4.5 * (cu + cU)) - du15;
+  return (R)L::w(i) * (drho * A + D);
+}
+
+template <int Q, class R>
+__device__ __forceinline__ R cdot(int i, R vx, R vy, R vz) {
+  using L = Lat<Q>;
+  R t = 0;
+  if (L::c(i, 0)) t += L::c(i, 0) > 0 ? vx : -vx;
+  if (L::c(i, 1)) t += L::c(i, 1) > 0 ? vy : -vy;
+  if (L::c(i, 2)) t += L::c(i, 2) > 0 ? vz : -vz;
+  return t;
+}
+
+template <int Q, class R>
+__device__ __forceinline__ R heq_dev(int i, R drho, R dux, R duy, R duz, R U, R uu15, R du15) {
+  return heq_cdu<Q, R>(i, cdot<Q, R>(i, dux, duy, duz), drho, U, (R)1 - uu15, du15);
 }
 
 // --------------------------------------------------------------------------
@@ -410,20 +520,25 @@ __device__ typename Compute<ST>::R pull_bc(const Params& p, int x, int y, int z,
   const int fi = sy < 0 ? 0 : 1;   // 0 = ymin, 1 = ymax
   const int kind = p.kind[YMIN + fi];
   if (kind == BC_FREESTREAM) {
-    const R ux = (R)p.u_face[YMIN + fi][0], uy = (R)p.u_face[YMIN + fi][1],
-            uz = (R)p.u_face[YMIN + fi][2];
-    const R cu = (R)cx * ux + (R)cy * uy + (R)cz * uz;
-    const R uu = ux * ux + uy * uy + uz * uz;
-    return (R)L::w(i) * ((R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
+    // incoming populations at f^eq(1, u_inf)
+    const R U = psel<R>(p.Ush, p.Ush_f);
+    const R ux = psel<R>(p.u_face[YMIN + fi][0], p.u_face_f[YMIN + fi][0]), uy = psel<R>(p.u_face[YMIN + fi][1], p.u_face_f[YMIN + fi][1]),
+            uz = psel<R>(p.u_face[YMIN + fi][2], p.u_face_f[YMIN + fi][2]);
+    const R dux = ux - U;
+    const R uu15 = (R)1.5 * (ux * ux + uy * uy + uz * uz);
+    const R du15 = (R)1.5 * (dux * ((R)2 * U + dux) + uy * uy + uz * uz);
+    return heq_dev<Q, R>(i, (R)0, dux, uy, uz, U, uu15, du15);
   }
   const bool wall_col = p.wall[fi] && x >= p.xw0[fi];
   if (wall_col && kind == BC_WALL_BB) {
-    // Eq. 31: f_i(B, t+1) = f*_{opp i}(B, t) + 2 w rho_w c_i.u_w / c_s^2
+    // Eq. 31: f_i(B, t+1) = f*_{opp i}(B, t) + 2 w rho_w c_i.u_w / c_s^2; in deviations
+    // E_{opp i} - E_i = -6 w c_x U adds to the reflected value
     const int node = z * (p.nx - p.xw0[fi]) + (x - p.xw0[fi]);
     const R* uw = (const R*)p.uw[fi] + 3 * node;
     const R cu = (R)cx * uw[0] + (R)cy * uw[1] + (R)cz * uw[2];
     const R rw = ((const R*)p.rhow[fi])[node];
-    return (R)C::ld(f + opp(i) * p.ncell + cidx(p, x, y, z)) + (R)6 * (R)L::w(i) * rw * cu;
+    return (R)C::ld(f + opp(i) * p.ncell + cidx(p, x, y, z)) +
+           (R)6 * (R)L::w(i) * (rw * cu - (R)cx * psel<R>(p.Ush, p.Ush_f));
   }
   if (wall_col) {  // HRFD: every population of B is rebuilt later
     *known = false;
@@ -434,9 +549,9 @@ __device__ typename Compute<ST>::R pull_bc(const Params& p, int x, int y, int z,
 }
 
 // --------------------------------------------------------------------------
-// Local collision in deviation form.
-//   rho = 1 + sum g, rho u = sum g c + F/2 (Eqs. 4-5)
-//   g^eq = w (drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u))
+// Local collision in deviation form (g below stands for h = f - E).
+//   rho = 1 + sum g, rho u = U x + sum g c + F/2 (Eqs. 4-5)
+//   g^eq = f^eq(rho, u) - E (heq_dev)
 //   BGK: g* = g - omega (g - g^eq) + (1 - omega/2) F_i
 //   regularized: g* = g^eq + (1 - omega) P(g - g^eq) + (1 - omega/2) F_i with
 //   P the Hermite projection up to second order.
@@ -463,63 +578,78 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
     if (L::c(i, 1)) jy += L::c(i, 1) > 0 ? g[i] : -g[i];
     if (L::c(i, 2)) jz += L::c(i, 2) > 0 ? g[i] : -g[i];
   }
-  const R Fx = (R)p.F[0], Fy = (R)p.F[1], Fz = (R)p.F[2];
+  // sum h c = rho u - U x - F/2: momentum relative to the reference velocity
+  const R Fx = psel<R>(p.F[0], p.F_f[0]), Fy = psel<R>(p.F[1], p.F_f[1]), Fz = psel<R>(p.F[2], p.F_f[2]);
   jx += (R)0.5 * Fx;
   jy += (R)0.5 * Fy;
   jz += (R)0.5 * Fz;
+  const R U = psel<R>(p.Ush, p.Ush_f);
   const R rho = (R)1 + drho;
-  const R inv = (R)1 / rho;
-  const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
+  const R inv = fdiv((R)1, rho);
+  const R dux = (jx - drho * U) * inv, uy = jy * inv, uz = jz * inv;
+  const R ux = U + dux;
   u_out[0] = ux;
   u_out[1] = uy;
   u_out[2] = uz;
-  const R uu15 = (R)1.5 * (ux * ux + uy * uy + uz * uz);
-  const R uF = ux * Fx + uy * Fy + uz * Fz;
+  const R one_m_uu15 = (R)1 - (R)1.5 * (ux * ux + uy * uy + uz * uz);
+  const R du15 = (R)1.5 * (dux * ((R)2 * U + dux) + uy * uy + uz * uz);
+  // (1 - omega/2) w [3 (c - u).F + 9 (c.u)(c.F)] = (delta/2) [A_i (1 + 3 c.u) - 3 w u.F]
   const R fpre = (R)0.5 * delta;
+  const R uF3 = (R)3 * (ux * Fx + uy * Fy + uz * Fz);
+  if (p.collision == 0) {
+    // BGK, one pass per direction
+    if (p.has_force) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const R cdu = cdot<Q, R>(i, dux, uy, uz);
+        const R geq = heq_cdu<Q, R>(i, cdu, drho, U, one_m_uu15, du15);
+        const R cu = (L::c(i, 0) > 0 ? U : (L::c(i, 0) < 0 ? -U : (R)0)) + cdu;
+        const R Fi = psel<R>(p.guoA[i], p.guoA_f[i]) * ((R)1 + (R)3 * cu) - (R)L::w(i) * uF3;
+        g[i] = ((R)2 * geq - g[i]) + delta * (g[i] - geq) + fpre * Fi;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const R geq = heq_cdu<Q, R>(i, cdot<Q, R>(i, dux, uy, uz), drho, U, one_m_uu15, du15);
+        g[i] = ((R)2 * geq - g[i]) + delta * (g[i] - geq);
+      }
+    }
+    return;
+  }
+  // regularized: non-equilibrium moments first, then the rebuilt populations
   R geq[Q];
 #pragma unroll
+  for (int i = 0; i < Q; ++i)
+    geq[i] = heq_cdu<Q, R>(i, cdot<Q, R>(i, dux, uy, uz), drho, U, one_m_uu15, du15);
+  R a[3] = {0, 0, 0}, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const R cu = (R)L::c(i, 0) * ux + (R)L::c(i, 1) * uy + (R)L::c(i, 2) * uz;
-    geq[i] = (R)L::w(i) * (drho + rho * ((R)3 * cu + (R)4.5 * cu * cu - uu15));
+    const R n = g[i] - geq[i];
+    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+    a[0] += (R)cx * n;
+    a[1] += (R)cy * n;
+    a[2] += (R)cz * n;
+    pxx += (R)(cx * cx) * n;
+    pyy += (R)(cy * cy) * n;
+    pzz += (R)(cz * cz) * n;
+    pxy += (R)(cx * cy) * n;
+    pxz += (R)(cx * cz) * n;
+    pyz += (R)(cy * cz) * n;
   }
-  if (p.collision == 0) {
+  const R tr = (pxx + pyy + pzz) * ((R)1 / (R)3);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = ((R)2 * geq[i] - g[i]) + delta * (g[i] - geq[i]);
-  } else {
-    R a[3] = {0, 0, 0}, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const R n = g[i] - geq[i];
-      const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-      a[0] += (R)cx * n;
-      a[1] += (R)cy * n;
-      a[2] += (R)cz * n;
-      pxx += (R)(cx * cx) * n;
-      pyy += (R)(cy * cy) * n;
-      pzz += (R)(cz * cz) * n;
-      pxy += (R)(cx * cy) * n;
-      pxz += (R)(cx * cz) * n;
-      pyz += (R)(cy * cz) * n;
+  for (int i = 0; i < Q; ++i) {
+    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+    const R qp = (R)(cx * cx) * pxx + (R)(cy * cy) * pyy + (R)(cz * cz) * pzz +
+                 (R)2 * ((R)(cx * cy) * pxy + (R)(cx * cz) * pxz + (R)(cy * cz) * pyz) - tr;
+    const R ca = (R)cx * a[0] + (R)cy * a[1] + (R)cz * a[2];
+    const R P = (R)L::w(i) * ((R)3 * ca + (R)4.5 * qp);
+    R gi = (geq[i] - P) + delta * P;
+    if (p.has_force) {
+      const R cu = (cx > 0 ? U : (cx < 0 ? -U : (R)0)) + cdot<Q, R>(i, dux, uy, uz);
+      gi += fpre * (psel<R>(p.guoA[i], p.guoA_f[i]) * ((R)1 + (R)3 * cu) - (R)L::w(i) * uF3);
     }
-    const R tr = (pxx + pyy + pzz) * ((R)1 / (R)3);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-      const R qp = (R)(cx * cx) * pxx + (R)(cy * cy) * pyy + (R)(cz * cz) * pzz +
-                   (R)2 * ((R)(cx * cy) * pxy + (R)(cx * cz) * pxz + (R)(cy * cz) * pyz) - tr;
-      const R ca = (R)cx * a[0] + (R)cy * a[1] + (R)cz * a[2];
-      const R P = (R)L::w(i) * ((R)3 * ca + (R)4.5 * qp);
-      g[i] = (geq[i] - P) + delta * P;
-    }
-  }
-  if (p.has_force) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-      const R cF = (R)cx * Fx + (R)cy * Fy + (R)cz * Fz;
-      const R cu = (R)cx * ux + (R)cy * uy + (R)cz * uz;
-      g[i] += fpre * (R)L::w(i) * ((R)3 * (cF - uF) + (R)9 * cu * cF);
-    }
+    g[i] = gi;
   }
 }
 

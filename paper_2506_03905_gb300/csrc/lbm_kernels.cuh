@@ -15,20 +15,105 @@
 namespace lbm {
 
 // ----------------------------------------------------------------------------
-// Bulk: one thread per cell, x fastest within a warp.
+// Cells with no non-periodic face within one cell: the six neighbour offsets
+// (periodic wrap folded in) replace all face logic; 32-bit indexing (the
+// lattice is checked at creation to satisfy Q * pitch * ny * nz < 2^31).
 // ----------------------------------------------------------------------------
 template <int Q, int ST>
-__global__ void __launch_bounds__(256) k_bulk(const Params p) {
+__device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int z) {
+  using L = Lat<Q>;
+  using C = Codec<ST>;
+  using R = typename Compute<ST>::R;
+  using T = typename C::T;
+  const T* __restrict__ fs = (const T*)p.f_src;
+  T* __restrict__ fd = (T*)p.f_dst;
+  const R* __restrict__ us = (const R*)p.u_src;
+  R* __restrict__ ud = (R*)p.u_dst;
+  const R* __restrict__ ns = (const R*)p.nt_src;
+  R* __restrict__ nd = (R*)p.nt_dst;
+  const int pitch = p.pitch;
+  const int plane = pitch * p.ny;
+  const int nc = (int)p.ncell;
+  const int id = (z * p.ny + y) * pitch + x;
+  // offsets to the neighbours at x-1, x+1, y-1, y+1, z-1, z+1
+  const int oxm = x == 0 ? p.nx - 1 : -1;
+  const int oxp = x == p.nx - 1 ? -(p.nx - 1) : 1;
+  const int oym = y == 0 ? (p.ny - 1) * pitch : -pitch;
+  const int oyp = y == p.ny - 1 ? -(p.ny - 1) * pitch : pitch;
+  const int ozm = z == 0 ? (p.nz - 1) * plane : -plane;
+  const int ozp = z == p.nz - 1 ? -(p.nz - 1) * plane : plane;
+
+  // 1. pull streaming (Eq. 3): source x - c_i; issued first so that the loads
+  //    are in flight while the SA stencil is evaluated
+  R g[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+    const int off = (cx > 0 ? oxm : (cx < 0 ? oxp : 0)) + (cy > 0 ? oym : (cy < 0 ? oyp : 0)) +
+                    (cz > 0 ? ozm : (cz < 0 ? ozp : 0));
+    g[i] = (R)C::ld(fs + (i * nc + id + off));
+  }
+
+  // 2. SA working variable of the new step (Eq. 11)
+  R ntn;
+  if (p.turbulent)
+    ntn = sa_update_interior<R, (Q == 19)>(p, ns, us, id, nc, oxm, oxp, oym, oyp, ozm, ozp, x, y);
+  else
+    ntn = ns[id];
+  nd[id] = ntn;
+  const R nu = psel<R>(p.nu, p.nu_f);
+  const R nut = p.turbulent ? sa_nut<R>(ntn, nu) : (R)0;
+  const R delta = relax_delta<R>((R)3 * (nu + nut));   // 2 - omega (Eq. 8)
+
+  // 3. moments and collision
+  R u[3];
+  collide<Q, R>(p, g, delta, u);
+
+  // 4. store
+#pragma unroll
+  for (int i = 0; i < Q; ++i) C::st(fd + (i * nc + id), g[i]);
+  ud[id] = u[0];
+  ud[id + nc] = u[1];
+  ud[id + 2 * nc] = u[2];
+}
+
+// ----------------------------------------------------------------------------
+// Bulk: one thread per cell, x fastest within a warp.  Cells next to a face
+// take the general path with the face rules.
+// ----------------------------------------------------------------------------
+// GENERAL = false: the launch holds only cells without a non-periodic face
+// within one cell (checked by the host), so the face logic is not compiled in.
+// Minimum resident blocks per SM requested from the compiler for k_bulk
+// (sets its register budget; 0 leaves the choice to the compiler).  Four
+// blocks of 256 threads (<= 64 registers) measured fastest on GB300 for the
+// D3Q19 FP32 channel: 0.159 ms against 0.172 ms with the compiler's 80.
+#ifndef LBM_BULK_MINB
+#define LBM_BULK_MINB 4
+#endif
+#if LBM_BULK_MINB > 0
+#define LBM_BULK_BOUNDS __launch_bounds__(256, LBM_BULK_MINB)
+#else
+#define LBM_BULK_BOUNDS __launch_bounds__(256)
+#endif
+
+template <int Q, int ST, bool GENERAL>
+__global__ void LBM_BULK_BOUNDS k_bulk(const Params p, int rows) {
   using L = Lat<Q>;
   using C = Codec<ST>;
   using R = typename Compute<ST>::R;
   using T = typename C::T;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int r = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x >= p.nx || y >= p.ny) return;
+  int y = r;
+  if (rows == ROWS_INNER) y = r + 1;
+  else if (rows == ROWS_WALL) y = r == 0 ? 0 : (r == 1 ? p.ny - 1 : p.ny);
+  if (x >= p.nx || y >= p.ny || (rows == ROWS_INNER && y >= p.ny - 1)) return;
+  if (!GENERAL || ((p.px || (x >= 1 && x <= p.nx - 2)) && (p.py || (y >= 1 && y <= p.ny - 2)))) {
+    bulk_interior<Q, ST>(p, x, y, z);
+    return;
+  }
   const long long id = cidx(p, x, y, z);
-  const T* __restrict__ fs = (const T*)p.f_src;
   T* __restrict__ fd = (T*)p.f_dst;
   const R* __restrict__ us = (const R*)p.u_src;
   R* __restrict__ ud = (R*)p.u_dst;
@@ -46,14 +131,14 @@ __global__ void __launch_bounds__(256) k_bulk(const Params p) {
     if (wf >= 0) {
       ntn = nd[id];
     } else {
-      ntn = inlet ? (R)p.nt_face[XMIN] : sa_update<R, (Q == 19)>(p, ns, us, x, y, z);
+      ntn = inlet ? psel<R>(p.nt_face[XMIN], p.nt_face_f[XMIN]) : sa_update<R, (Q == 19)>(p, ns, us, x, y, z);
       nd[id] = ntn;
     }
   } else {
     ntn = ns[id];
     nd[id] = ntn;
   }
-  const R nu = (R)p.nu;
+  const R nu = psel<R>(p.nu, p.nu_f);
   const R nut = p.turbulent ? sa_nut<R>(ntn, nu) : (R)0;
   const R delta = relax_delta<R>((R)3 * (nu + nut));   // 2 - omega (Eq. 8)
 
@@ -64,15 +149,6 @@ __global__ void __launch_bounds__(256) k_bulk(const Params p) {
     const R* fr = (const R*)p.frec[wf] + (long long)node * Q;
 #pragma unroll
     for (int i = 0; i < Q; ++i) g[i] = fr[i];
-  } else if (x >= 1 && x <= p.nx - 2 && y >= 1 && y <= p.ny - 2) {
-    const int zm = z == 0 ? p.nz - 1 : z - 1;
-    const int zp = z == p.nz - 1 ? 0 : z + 1;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int cz = L::c(i, 2);
-      const int sz = cz == 0 ? z : (cz > 0 ? zm : zp);
-      g[i] = (R)C::ld(fs + i * p.ncell + cidx(p, x - L::c(i, 0), y - L::c(i, 1), sz));
-    }
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -82,7 +158,7 @@ __global__ void __launch_bounds__(256) k_bulk(const Params p) {
     if (inlet) {
       // Zou-He velocity inlet: unknowns c_x > 0 from the non-equilibrium
       // bounce-back of the normal direction plus transverse corrections.
-      const R ux = (R)p.u_face[XMIN][0], uy = (R)p.u_face[XMIN][1], uz = (R)p.u_face[XMIN][2];
+      const R ux = psel<R>(p.u_face[XMIN][0], p.u_face_f[XMIN][0]), uy = psel<R>(p.u_face[XMIN][1], p.u_face_f[XMIN][1]), uz = psel<R>(p.u_face[XMIN][2], p.u_face_f[XMIN][2]);
       R s0 = 0, sm = 0, ky = 0, kz = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -94,14 +170,18 @@ __global__ void __launch_bounds__(256) k_bulk(const Params p) {
           sm += g[i];
         }
       }
-      const R rho = ((R)1 + s0 + (R)2 * sm) / ((R)1 - ux);
-      const R Ny = (R)0.5 * ky - rho * uy / (R)3;
-      const R Nz = (R)0.5 * kz - rho * uz / (R)3;
+      // in deviations from E = f^eq(1, U x): sum_{cx=0} E + 2 sum_{cx<0} E = 1 - U and
+      // E_{opp i} - E_i = -6 w c_x U
+      const R U = psel<R>(p.Ush, p.Ush_f);
+      const R rho = fdiv(((R)1 - U) + s0 + (R)2 * sm, (R)1 - ux);
+      const R Ny = (R)0.5 * ky - rho * uy * (R)(1.0 / 3.0);
+      const R Nz = (R)0.5 * kz - rho * uz * (R)(1.0 / 3.0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         if (L::c(i, 0) > 0) {
           const R cu = (R)L::c(i, 0) * ux + (R)L::c(i, 1) * uy + (R)L::c(i, 2) * uz;
-          g[i] = g[opp(i)] + (R)6 * (R)L::w(i) * rho * cu - (R)L::c(i, 1) * Ny - (R)L::c(i, 2) * Nz;
+          g[i] = g[opp(i)] + (R)6 * (R)L::w(i) * (rho * cu - (R)L::c(i, 0) * U) -
+                 (R)L::c(i, 1) * Ny - (R)L::c(i, 2) * Nz;
         }
       }
     }
@@ -175,7 +255,7 @@ __global__ void __launch_bounds__(128) k_wall(const Params p) {
   } else {
     // Section 3.1: regularized node with the HRFD gradient
     const int yF = yB + s, yFF = yB + 2 * s;
-    R jF[3] = {(R)0.5 * (R)p.F[0], (R)0.5 * (R)p.F[1], (R)0.5 * (R)p.F[2]};
+    R jF[3] = {(R)0.5 * psel<R>(p.F[0], p.F_f[0]), (R)0.5 * psel<R>(p.F[1], p.F_f[1]), (R)0.5 * psel<R>(p.F[2], p.F_f[2])};
     R rhoF = (R)1;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -186,7 +266,7 @@ __global__ void __launch_bounds__(128) k_wall(const Params p) {
       jF[1] += (R)L::c(i, 1) * gi;
       jF[2] += (R)L::c(i, 2) * gi;
     }
-    const double Ux = (double)(jF[0] / rhoF), Uz = (double)(jF[2] / rhoF);
+    const double Ux = ((double)jF[0] + p.Ush) / (double)rhoF, Uz = (double)(jF[2] / rhoF);
     const double U = sqrt(Ux * Ux + Uz * Uz);
     const double tx = U > 0.0 ? Ux / U : 1.0, tz = U > 0.0 ? Uz / U : 0.0;
     if (p.turbulent)
@@ -240,13 +320,15 @@ __global__ void __launch_bounds__(128) k_wall(const Params p) {
     const R Sxy = (R)0.5 * (G[0][1] + G[1][0]), Sxz = (R)0.5 * (G[0][2] + G[2][0]),
             Syz = (R)0.5 * (G[1][2] + G[2][1]);
     const R trS = (Sxx + Syy + Szz) / (R)3;
+    const R Us = psel<R>(p.Ush, p.Ush_f);
+    const R dux = (R)(upB * tx - p.Ush);
     const R uu15 = (R)1.5 * (uB[0] * uB[0] + uB[2] * uB[2]);
+    const R du15 = (R)1.5 * (dux * ((R)2 * Us + dux) + uB[2] * uB[2]);
     R* fr = (R*)p.frec[fi] + (long long)node * Q;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-      const R cu = (R)cx * uB[0] + (R)cz * uB[2];
-      const R geq = (R)L::w(i) * ((rhoB - (R)1) + rhoB * ((R)3 * cu + (R)4.5 * cu * cu - uu15));
+      const R geq = heq_dev<Q, R>(i, rhoB - (R)1, dux, (R)0, uB[2], Us, uu15, du15);
       const R qs = (R)(cx * cx) * Sxx + (R)(cy * cy) * Syy + (R)(cz * cz) * Szz +
                    (R)2 * ((R)(cx * cy) * Sxy + (R)(cx * cz) * Sxz + (R)(cy * cz) * Syz) - trS;
       fr[i] = geq - (R)3 * (R)L::w(i) * rhoB * tau * qs;     // Eqs. 19, 26
@@ -274,15 +356,16 @@ __global__ void k_init(const Params p, const double* rho, const double* u, const
     const int y = (int)((k / p.nx) % p.ny);
     const int z = (int)(k / ((long long)p.nx * p.ny));
     const long long id = cidx(p, x, y, z);
-    const R r = (R)(rho[k] / rho0);
-    const R ux = (R)(u[k] * ucv), uy = (R)(u[k + n] * ucv), uz = (R)(u[k + 2 * n] * ucv);
+    const double uxd = u[k] * ucv;
+    const R drho = (R)(rho[k] / rho0 - 1.0);
+    const R ux = (R)uxd, uy = (R)(u[k + n] * ucv), uz = (R)(u[k + 2 * n] * ucv);
+    const R U = psel<R>(p.Ush, p.Ush_f);
+    const R dux = (R)(uxd - p.Ush);
     const R uu15 = (R)1.5 * (ux * ux + uy * uy + uz * uz);
+    const R du15 = (R)1.5 * (dux * ((R)2 * U + dux) + uy * uy + uz * uz);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const R cu = (R)L::c(i, 0) * ux + (R)L::c(i, 1) * uy + (R)L::c(i, 2) * uz;
-      const R geq = (R)L::w(i) * ((r - (R)1) + r * ((R)3 * cu + (R)4.5 * cu * cu - uu15));
-      C::st((T*)p.f_dst + i * p.ncell + id, geq);
-    }
+    for (int i = 0; i < Q; ++i)
+      C::st((T*)p.f_dst + i * p.ncell + id, heq_dev<Q, R>(i, drho, dux, uy, uz, U, uu15, du15));
     R* ud = (R*)p.u_dst;
     ud[id] = ux;
     ud[id + p.ncell] = uy;

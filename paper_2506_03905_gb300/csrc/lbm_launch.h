@@ -5,8 +5,9 @@
 
 namespace lbm {
 #define LBM_DECLARE_LAUNCHERS(Q)                                                               \
-  void launch_bulk_q##Q(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s);              \
-  void launch_wall_q##Q(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s);              \
+  void launch_bulk_q##Q(int st, const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s,     \
+                        int prio);                                                             \
+  void launch_wall_q##Q(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio);    \
   void launch_init_q##Q(int st, const Params& p, int grid, const double* rho, const double* u, \
                         const double* nt, double rho0, double ucv, double nucv, cudaStream_t s); \
   void launch_fields_q##Q(int st, const Params& p, int grid, double* rho, double* u,          \

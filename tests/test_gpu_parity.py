@@ -162,6 +162,26 @@ def test_checkpoint_resume_bit_exact():
     assert np.array_equal(ua["u"], uc["u"]) and np.array_equal(ua["nu_tilde"], uc["nu_tilde"])
 
 
+@pytest.mark.parametrize("scheme", ["wall_bb", "wall_hrfd"])
+def test_timed_sequential_and_graph_forked_steps_agree_bit_exact(scheme):
+    """lbm_step_timed runs wall pre-pass and bulk one after the other; lbm_step
+    overlaps the wall pre-pass with the inner rows: same per-cell arithmetic."""
+    import paper_2506_03905_gb300 as pkg
+    case = C.channel_3d(scheme=scheme, nx=40, ny=20, nz=3)
+    out = []
+    for timed in (False, True):
+        s = pkg.Solver(case)
+        s.set_fields(*C.initial_fields(case))
+        if timed:
+            s.step_timed(10)
+        else:
+            s.step(10)
+        out.append(s.fields(["u", "nu_tilde", "u_tau_ymin"]))
+        s.close()
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
 def test_graph_and_single_steps_agree_bit_exact():
     case = C.channel_3d(scheme="wall_bb", nx=24, ny=12, nz=3)
     a = run_gpu(case, 9)

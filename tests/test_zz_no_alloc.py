@@ -33,8 +33,10 @@ def _state_populations(solver, case):
 def test_noalloc_moments_match_diagnostics_twice(storage):
     import torch
     import paper_2506_03905_gb300 as pkg
+    # populations stored as f_i - w_i (no reference-velocity shift), the layout
+    # the entry point documents
     case = C.channel_3d(re_tau=5200.0, scheme="wall_bb", nx=40, ny=20, nz=5, seed=3,
-                        storage=storage)
+                        storage=storage).replace(u_shift=0.0)
     s = pkg.Solver(case)
     s.set_fields(*C.initial_fields(case))
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
