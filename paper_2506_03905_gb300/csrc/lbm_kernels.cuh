@@ -96,19 +96,13 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
 #define LBM_BULK_BOUNDS __launch_bounds__(256)
 #endif
 
+// One cell of the bulk update (every cell of the lattice takes this path).
 template <int Q, int ST, bool GENERAL>
-__global__ void LBM_BULK_BOUNDS k_bulk(const Params p, int rows) {
+__device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) {
   using L = Lat<Q>;
   using C = Codec<ST>;
   using R = typename Compute<ST>::R;
   using T = typename C::T;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  int y = r;
-  if (rows == ROWS_INNER) y = r + 1;
-  else if (rows == ROWS_WALL) y = r == 0 ? 0 : (r == 1 ? p.ny - 1 : p.ny);
-  if (x >= p.nx || y >= p.ny || (rows == ROWS_INNER && y >= p.ny - 1)) return;
   if (!GENERAL || ((p.px || (x >= 1 && x <= p.nx - 2)) && (p.py || (y >= 1 && y <= p.ny - 2)))) {
     bulk_interior<Q, ST>(p, x, y, z);
     return;
@@ -199,19 +193,27 @@ __global__ void LBM_BULK_BOUNDS k_bulk(const Params p, int rows) {
   ud[id + 2 * p.ncell] = u[2];
 }
 
+template <int Q, int ST, bool GENERAL>
+__global__ void LBM_BULK_BOUNDS k_bulk(const Params p, int rows) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  int y = r;
+  if (rows == ROWS_INNER) y = r + 1;
+  else if (rows == ROWS_WALL) y = r == 0 ? 0 : (r == 1 ? p.ny - 1 : p.ny);
+  if (x >= p.nx || y >= p.ny || (rows == ROWS_INNER && y >= p.ny - 1)) return;
+  bulk_cell<Q, ST, GENERAL>(p, x, y, z);
+}
+
 // ----------------------------------------------------------------------------
-// Wall pre-pass: one thread per wall node; blockIdx.y selects the y face.
+// Wall pre-pass: one thread per wall node of face fi (0 = ymin, 1 = ymax).
 // ----------------------------------------------------------------------------
 template <int Q, int ST>
-__global__ void __launch_bounds__(128) k_wall(const Params p) {
+__device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
   using L = Lat<Q>;
   using C = Codec<ST>;
   using R = typename Compute<ST>::R;
   using T = typename C::T;
-  const int fi = blockIdx.y;
-  if (!p.wall[fi]) return;
-  const int node = blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= p.nwall[fi]) return;
   const int nwx = p.nx - p.xw0[fi];
   const int z = node / nwx;
   const int x = p.xw0[fi] + node % nwx;
@@ -337,6 +339,15 @@ __global__ void __launch_bounds__(128) k_wall(const Params p) {
   }
   p.utau[fi][node] = ut;
   if (!ok) atomicOr(p.flags, FLAG_NEWTON);
+}
+
+template <int Q, int ST>
+__global__ void __launch_bounds__(128) k_wall(const Params p) {
+  const int fi = blockIdx.y;
+  if (!p.wall[fi]) return;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= p.nwall[fi]) return;
+  wall_node<Q, ST>(p, fi, node);
 }
 
 // ----------------------------------------------------------------------------
