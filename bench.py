@@ -242,7 +242,7 @@ def run_ours(args):
 
     # ---- variants on the same GPU (rank 0 only, short)
     variants = {}
-    if rank == 0 and not args.no_variants:
+    if world == 1 and not args.no_variants:
         vsteps = max(10, min(args.steps, 100))
         for label, kw in [("fp32_hrfd", dict(scheme="wall_hrfd", storage="fp32")),
                           ("fp16_bb", dict(storage="fp16")), ("bf16_bb", dict(storage="bf16")),
@@ -296,8 +296,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def batched_variant(pkg, torch, steps):
+def batched_variant(pkg, torch, steps, rank=0, world=1):
     cases = C.batched_sweep(96, storage="fp32")
+    if world > 1:   # instances are independent: each rank advances its own shard
+        mine = C.shard_instances([c.cells for c in cases], world, rank)
+        cases = [cases[i] for i in mine]
     solvers = []
     for c in cases:
         s = pkg.Solver(c)

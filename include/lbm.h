@@ -60,7 +60,10 @@ enum {
   LBM_BC_SYMMETRY = 3,         /* specular reflection (free slip) */
   LBM_BC_INLET_ZOUHE = 4,      /* Zou-He velocity inlet (xmin only) */
   LBM_BC_OUTLET_ZEROGRAD = 5,  /* zero-gradient outlet (xmax only) */
-  LBM_BC_FREESTREAM = 6        /* incoming populations at f^eq(rho0, u_in) */
+  LBM_BC_FREESTREAM = 6,       /* incoming populations at f^eq(rho0, u_in) */
+  LBM_BC_WALL_CAI_DEGRIGNY = 7 /* Section 3.1.2: regularized wall (Eqs. 19, 23, 26) whose
+                                  wall-normal gradient is the third-order difference of
+                                  the wall function, Eqs. 29-30 */
 };
 
 /* faces (lbm_set_bc face argument) */

@@ -31,7 +31,7 @@ import numpy as np
 
 FACES = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
 BC_KINDS = ("periodic", "wall_bb", "wall_hrfd", "symmetry", "inlet_zouhe",
-            "outlet_zerograd", "freestream")
+            "outlet_zerograd", "freestream", "wall_cai_degrigny")
 
 NU_AIR = 1.5e-5          # m^2/s, Section 4.1.1 and Section 4.2.1
 RHO0 = 1.0               # kg/m^3, Section 4.1.1
@@ -263,3 +263,22 @@ def batched_sweep(n: int = 96, seed: int = 2506, storage: str = "fp32") -> List[
                           lattice=lattice)
         out.append(c)
     return out
+
+
+def shard_instances(cells: List[int], world: int, rank: int) -> List[int]:
+    """Indices of the instances rank `rank` of `world` advances in a sharded sweep.
+
+    Instances are independent, so a sweep shards with no exchange between ranks:
+    greedy longest-first assignment of instances to the rank with the fewest
+    cells so far (ties to the lower rank), which keeps the per-rank cell counts
+    within one instance of each other.
+    """
+    if world < 1 or not (0 <= rank < world):
+        raise ValueError("bad rank / world size")
+    load = [0] * world
+    owner = [0] * len(cells)
+    for i in sorted(range(len(cells)), key=lambda k: (-cells[k], k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += cells[i]
+    return [i for i in range(len(cells)) if owner[i] == rank]

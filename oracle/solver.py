@@ -69,7 +69,8 @@ class Oracle:
             if (a == "periodic") != (b == "periodic"):
                 raise ValueError(f"{ax} faces: periodic must be paired")
         for f in ("xmin", "xmax"):
-            if bcs[f].kind in ("wall_bb", "wall_hrfd", "symmetry", "freestream"):
+            if bcs[f].kind in ("wall_bb", "wall_hrfd", "wall_cai_degrigny", "symmetry",
+                               "freestream"):
                 raise ValueError("x faces: periodic, inlet or outlet only")
         if bcs["xmin"].kind == "outlet_zerograd" or bcs["xmax"].kind == "inlet_zouhe":
             raise ValueError("inlet on xmin, outlet on xmax only")
@@ -97,7 +98,7 @@ class Oracle:
         self.xc = case.origin[0] + (np.arange(self.nx) + 0.5) * case.dx
         self.walls = {}
         for f in ("ymin", "ymax"):
-            if bcs[f].kind in ("wall_bb", "wall_hrfd"):
+            if bcs[f].kind in ("wall_bb", "wall_hrfd", "wall_cai_degrigny"):
                 self.walls[f] = self.xc >= bcs[f].x_start
         self.inv_d2 = self._inv_wall_distance_sq()
         self.utau = {f: np.zeros((self.nz, self.nx)) for f in self.walls}
@@ -146,7 +147,7 @@ class Oracle:
             ghost[axi] = 0 if lo else -1
             inner[axi] = 1 if lo else -2
             g, i = tuple(ghost), tuple(inner)
-            if b.kind in ("symmetry", "wall_bb", "wall_hrfd"):
+            if b.kind in ("symmetry", "wall_bb", "wall_hrfd", "wall_cai_degrigny"):
                 ntp[g] = ntp[i]
                 for c in range(3):
                     up[(c,) + g] = up[(c,) + i] * (-1.0 if c == _AX[ax] else 1.0)
@@ -296,15 +297,27 @@ class Oracle:
                 f[j][:, :, -1] = f[j][:, :, -2]
         return f
 
+    def cai_degrigny_derivative(self, ut):
+        """Eq. 29: third-order one-sided difference of the wall function at B,
+        (u_tau / Delta) (-11/6 u+(y_B+) + 3 u+(y_B+ + D+) - 3/2 u+(y_B+ + 2 D+)
+        + 1/3 u+(y_B+ + 3 D+)), Delta = 1 (lattice), D+ = u_tau / nu."""
+        yp = ut * 0.5 / self.nu
+        dp = ut / self.nu
+        up = self.law.u_plus
+        return ut * (-11.0 / 6.0 * up(yp) + 3.0 * up(yp + dp) - 1.5 * up(yp + 2 * dp)
+                     + up(yp + 3 * dp) / 3.0)
+
     def hrfd(self, f, nt_new):
-        """Stage 6: regularized wall nodes with the HRFD gradient (Section 3.1)."""
+        """Stage 6: regularized wall nodes with the HRFD gradient (Section 3.1),
+        or with the Cai-Degrigny gradient (Section 3.1.2, Eq. 29)."""
         vs = self.vs
         Q = L.second_order_Q(vs)
         _, up = self._pad(self.nt, self.u)
         for face, cols in self.walls.items():
             b = self.bc[face]
-            if b.kind != "wall_hrfd":
+            if b.kind not in ("wall_hrfd", "wall_cai_degrigny"):
                 continue
+            cai = b.kind == "wall_cai_degrigny"
             row, s = self._row(face), self._inward(face)
             F_, FF = row + s, row + 2 * s
             n_y = -1.0 if face == "ymin" else 1.0
@@ -342,7 +355,9 @@ class Oracle:
                 uFn = up[g][1:-1, yF, 1:-1][:, cols]
                 uFFn = up[g][1:-1, yFF, 1:-1][:, cols]
                 fd = 0.5 * (-3.0 * uBn + 4.0 * uFn - uFFn)          # Eq. 28
-                if g != 1 and self.turbulent:
+                if g != 1 and self.turbulent and cai:
+                    dn = self.cai_degrigny_derivative(ut) * t[g]          # Eqs. 29-30
+                elif g != 1 and self.turbulent:
                     ana = np.where(ut > 0, ut * ut / self.nu * dup, 0.0) * t[g]   # Eq. 15
                     dn = b.beta * ana + (1.0 - b.beta) * fd               # Eq. 27
                 else:

@@ -41,7 +41,7 @@ STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2, "fp64": 3}
 TURBULENCE = {"sa": 0, "laminar": 1}
 WALL_LAW = {"sa_analytic": 0, "log": 1}
 BC_KIND = {"periodic": 0, "wall_bb": 1, "wall_hrfd": 2, "symmetry": 3, "inlet_zouhe": 4,
-           "outlet_zerograd": 5, "freestream": 6}
+           "outlet_zerograd": 5, "freestream": 6, "wall_cai_degrigny": 7}
 FACES = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
 FIELD = {"rho": 1 << 0, "u": 1 << 1, "nu_t": 1 << 2, "nu_tilde": 1 << 3,
          "u_tau_ymin": 1 << 4, "u_tau_ymax": 1 << 5, "cf_ymin": 1 << 6, "cf_ymax": 1 << 7}

@@ -230,12 +230,13 @@ extern "C" lbm_status lbm_set_bc(lbm_ctx* c, int face, const lbm_bc* bc) {
     return LBM_EINVAL;
   }
   const int kd = bc->kind;
-  if (kd < LBM_BC_PERIODIC || kd > LBM_BC_FREESTREAM) {
+  if (kd < LBM_BC_PERIODIC || kd > LBM_BC_WALL_CAI_DEGRIGNY) {
     lbm_ctx_set_error(c, "unknown boundary kind %d", kd);
     return LBM_EINVAL;
   }
   const bool xf = face <= LBM_XMAX, yf = face == LBM_YMIN || face == LBM_YMAX;
-  const bool wall = kd == LBM_BC_WALL_SLIP_BB || kd == LBM_BC_WALL_HRFD;
+  const bool wall = kd == LBM_BC_WALL_SLIP_BB || kd == LBM_BC_WALL_HRFD ||
+                    kd == LBM_BC_WALL_CAI_DEGRIGNY;
   if (face >= LBM_ZMIN && kd != LBM_BC_PERIODIC) {
     lbm_ctx_set_error(c, "z faces must be periodic");
     return LBM_EUNSUPPORTED;
@@ -257,8 +258,8 @@ extern "C" lbm_status lbm_set_bc(lbm_ctx* c, int face, const lbm_bc* bc) {
     lbm_ctx_set_error(c, "ref_node must be 1 (B) or 2 (F)");
     return LBM_EINVAL;
   }
-  if (kd == LBM_BC_WALL_HRFD && bc->ref_node != 2) {
-    lbm_ctx_set_error(c, "HRFD takes its reference velocity at F (ref_node = 2)");
+  if ((kd == LBM_BC_WALL_HRFD || kd == LBM_BC_WALL_CAI_DEGRIGNY) && bc->ref_node != 2) {
+    lbm_ctx_set_error(c, "regularized walls take their reference velocity at F (ref_node = 2)");
     return LBM_EINVAL;
   }
   if (kd == LBM_BC_WALL_HRFD && !(bc->beta >= 0.0 && bc->beta <= 1.0)) {
@@ -312,7 +313,8 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
   int nhrfd = 0;
   for (int fi = 0; fi < 2; ++fi) {
     const lbm_bc& b = c->bc[LBM_YMIN + fi];
-    const bool wall = b.kind == LBM_BC_WALL_SLIP_BB || b.kind == LBM_BC_WALL_HRFD;
+    const bool wall = b.kind == LBM_BC_WALL_SLIP_BB || b.kind == LBM_BC_WALL_HRFD ||
+                      b.kind == LBM_BC_WALL_CAI_DEGRIGNY;
     p.wall[fi] = 0;
     if (!wall) continue;
     int x0 = 0;
@@ -323,7 +325,7 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
     p.ref_node[fi] = b.ref_node;
     p.nwall[fi] = (c->nx - x0) * c->nz;
     if (p.nwall[fi] > 0) p.wall[fi] = b.kind;
-    if (b.kind == LBM_BC_WALL_HRFD) ++nhrfd;
+    if (b.kind == LBM_BC_WALL_HRFD || b.kind == LBM_BC_WALL_CAI_DEGRIGNY) ++nhrfd;
     if (c->ny < 3) {
       lbm_ctx_set_error(c, "walls need ny >= 3 (nodes B, F, FF)");
       return LBM_EINVAL;
@@ -334,7 +336,7 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
     }
   }
   if (nhrfd == 2 && c->ny < 6) {
-    lbm_ctx_set_error(c, "two HRFD walls need ny >= 6");
+    lbm_ctx_set_error(c, "two regularized walls need ny >= 6");
     return LBM_EINVAL;
   }
   const int pf[4] = {LBM_XMIN, LBM_XMAX, LBM_YMIN, LBM_YMAX};

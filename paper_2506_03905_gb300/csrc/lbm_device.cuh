@@ -21,7 +21,7 @@ namespace lbm {
 
 enum BcKind {
   BC_PERIODIC = 0, BC_WALL_BB = 1, BC_WALL_HRFD = 2, BC_SYMMETRY = 3,
-  BC_INLET = 4, BC_OUTLET = 5, BC_FREESTREAM = 6
+  BC_INLET = 4, BC_OUTLET = 5, BC_FREESTREAM = 6, BC_WALL_CAI = 7
 };
 enum { XMIN = 0, XMAX = 1, YMIN = 2, YMAX = 3 };
 enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2, ST_FP64 = 3 };
@@ -540,7 +540,7 @@ __device__ typename Compute<ST>::R pull_bc(const Params& p, int x, int y, int z,
     return (R)C::ld(f + opp(i) * p.ncell + cidx(p, x, y, z)) +
            (R)6 * (R)L::w(i) * (rw * cu - (R)cx * psel<R>(p.Ush, p.Ush_f));
   }
-  if (wall_col) {  // HRFD: every population of B is rebuilt later
+  if (wall_col) {  // regularized walls: every population of B is rebuilt later
     *known = false;
     return (R)0;
   }
@@ -597,22 +597,39 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
   const R fpre = (R)0.5 * delta;
   const R uF3 = (R)3 * (ux * Fx + uy * Fy + uz * Fz);
   if (p.collision == 0) {
-    // BGK, one pass per direction
-    if (p.has_force) {
+    // BGK over opposite pairs (i, i+1 = opp i): with s = c_i.u the equilibrium
+    // and force terms split into parts even and odd in c, so that
+    //   h^eq_{i / opp} = w [drho (e_A +/- 3 s) + (e_D +/- 3 c.du)],
+    //   e_A = 1 + 4.5 s^2 - 1.5 u.u,  e_D = 4.5 c.du (s + c_x U) - du15,
+    //   F_{i / opp} = 3 s A_i - 3 w u.F  +/-  A_i      (A_i = 3 w c_i.F)
+    const R wgt0 = (R)L::w(0);
+    {
+      const R geq = wgt0 * (drho * one_m_uu15 - du15);
+      R gi = ((R)2 * geq - g[0]) + delta * (g[0] - geq);
+      if (p.has_force) gi -= fpre * wgt0 * uF3;
+      g[0] = gi;
+    }
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const R cdu = cdot<Q, R>(i, dux, uy, uz);
-        const R geq = heq_cdu<Q, R>(i, cdu, drho, U, one_m_uu15, du15);
-        const R cu = (L::c(i, 0) > 0 ? U : (L::c(i, 0) < 0 ? -U : (R)0)) + cdu;
-        const R Fi = psel<R>(p.guoA[i], p.guoA_f[i]) * ((R)1 + (R)3 * cu) - (R)L::w(i) * uF3;
-        g[i] = ((R)2 * geq - g[i]) + delta * (g[i] - geq) + fpre * Fi;
+    for (int i = 1; i < Q; i += 2) {
+      const R w = (R)L::w(i);
+      const R cdu = cdot<Q, R>(i, dux, uy, uz);
+      const R cU = L::c(i, 0) > 0 ? U : (L::c(i, 0) < 0 ? -U : (R)0);
+      const R su = cU + cdu;                                   // c_i . u
+      const R eA = (R)4.5 * su * su + one_m_uu15;
+      const R eD = (R)4.5 * cdu * (su + cU) - du15;
+      const R ev = w * (drho * eA + eD);
+      const R od = w * (R)3 * (drho * su + cdu);
+      const R gp = ev + od, gm = ev - od;                      // h^eq_i, h^eq_opp
+      R np_ = ((R)2 * gp - g[i]) + delta * (g[i] - gp);
+      R nm_ = ((R)2 * gm - g[i + 1]) + delta * (g[i + 1] - gm);
+      if (p.has_force) {
+        const R A = psel<R>(p.guoA[i], p.guoA_f[i]);
+        const R fe = fpre * ((R)3 * su * A - w * uF3), fo = fpre * A;
+        np_ += fe + fo;
+        nm_ += fe - fo;
       }
-    } else {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const R geq = heq_cdu<Q, R>(i, cdot<Q, R>(i, dux, uy, uz), drho, U, one_m_uu15, du15);
-        g[i] = ((R)2 * geq - g[i]) + delta * (g[i] - geq);
-      }
+      g[i] = np_;
+      g[i + 1] = nm_;
     }
     return;
   }

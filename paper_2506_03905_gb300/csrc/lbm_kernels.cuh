@@ -138,7 +138,7 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
 
   // 2. post-stream populations
   R g[Q];
-  if (wf >= 0 && p.wall[wf] == BC_WALL_HRFD) {
+  if (wf >= 0 && p.wall[wf] != BC_WALL_BB) {   // regularized wall: rebuilt populations
     const int node = z * (p.nx - p.xw0[wf]) + (x - p.xw0[wf]);
     const R* fr = (const R*)p.frec[wf] + (long long)node * Q;
 #pragma unroll
@@ -303,10 +303,24 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
       G[2][0] = G[2][1] = G[2][2] = (R)0;
     }
     const long long idF = cidx(p, x, yF, z), idFF = cidx(p, x, yFF, z);
-    const double dup = ypB > 0.0 ? wf_dudy(p.wall_law, p.law_kappa, ypB) : 1.0;
-    const double ana = ut > 0.0 ? ut * ut / nu * dup : 0.0;   // Eq. 15
+    const bool cai = p.wall[fi] == BC_WALL_CAI;
+    double ana;
+    if (cai) {
+      // Eq. 29: (u_tau / Delta)(-11/6 u+(y_B+) + 3 u+(y_B+ + D+) - 3/2 u+(y_B+ + 2D+)
+      //          + 1/3 u+(y_B+ + 3D+)), Delta = 1, D+ = u_tau / nu
+      const double dp = ut / nu;
+      ana = ut > 0.0
+                ? ut * (-11.0 / 6.0 * wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB) +
+                        3.0 * wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB + dp) -
+                        1.5 * wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB + 2.0 * dp) +
+                        wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB + 3.0 * dp) / 3.0)
+                : 0.0;
+    } else {
+      const double dup = ypB > 0.0 ? wf_dudy(p.wall_law, p.law_kappa, ypB) : 1.0;
+      ana = ut > 0.0 ? ut * ut / nu * dup : 0.0;   // Eq. 15
+    }
     const double tdir[3] = {tx, 0.0, tz};
-    const R beta = (R)p.beta[fi];
+    const R beta = cai ? (R)1 : (R)p.beta[fi];     // Eq. 30: beta = 1 with Eq. 29
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const R fd = (R)0.5 * ((R)-3 * us[idB + c * p.ncell] + (R)4 * us[idF + c * p.ncell] -

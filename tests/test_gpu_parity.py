@@ -32,7 +32,7 @@ def run_gpu(case, nsteps, fields=None, split=None):
         s.step(nsteps)
     names = ["rho", "u", "nu_t", "nu_tilde"]
     for f in ("ymin", "ymax"):
-        if case.bcs[f].kind in ("wall_bb", "wall_hrfd"):
+        if case.bcs[f].kind in ("wall_bb", "wall_hrfd", "wall_cai_degrigny"):
             names += ["u_tau_" + f, "cf_" + f]
     out = s.fields(names)
     s.close()
@@ -61,7 +61,7 @@ def test_half_channel_2d_log_law(storage):
     compare(case, 400, TOL[storage])
 
 
-@pytest.mark.parametrize("scheme", ["wall_bb", "wall_hrfd"])
+@pytest.mark.parametrize("scheme", ["wall_bb", "wall_hrfd", "wall_cai_degrigny"])
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
 def test_channel_3d(scheme, storage):
     case = C.channel_3d(re_tau=5200.0, scheme=scheme, nx=40, ny=20, nz=5, seed=2,
@@ -77,7 +77,7 @@ def test_channel_3d_regularized_ref_b(scheme):
     compare(case, 100, TOL["fp32"])
 
 
-@pytest.mark.parametrize("scheme", ["wall_bb", "wall_hrfd"])
+@pytest.mark.parametrize("scheme", ["wall_bb", "wall_hrfd", "wall_cai_degrigny"])
 @pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
 def test_flat_plate(scheme, lattice):
     nz = 1 if lattice == "D2Q9" else 3

@@ -269,3 +269,28 @@ def test_acoustic_scaling():
     tau = 0.5 + math.sqrt(3.0) * c.mach / (re_l * c.dx / 1.0)
     assert 0.5 + 3.0 * o.nu == pytest.approx(tau, rel=1e-13)
     assert o.ucv * c.u_ref == pytest.approx(c.mach / math.sqrt(3.0), rel=1e-15)
+
+
+def test_cai_degrigny_ratio_fig5():
+    """Eq. 29 / Eq. 15 at y_B lies in the range the paper reports (0.76-0.77),
+    to within 0.005 at the finest grid of the low-Re curve."""
+    for re_tau, n0, n1, lo, hi in golden("fig5_cai_degrigny_ratio.txt"):
+        for n in range(int(n0), int(n1) + 1, 5):
+            c = C.half_channel_2d(re_tau=re_tau, ny=n, nx=4).replace(
+                wall_law="sa_analytic", bcs={"ymin": C.BC("wall_cai_degrigny")})
+            o = make(c)
+            ut = re_tau * c.nu / 1.0 * o.ucv            # target u_tau in lattice units
+            ypb = ut * 0.5 / o.nu
+            ratio = o.cai_degrigny_derivative(ut) / (ut * ut / o.nu * W.dudy_plus_sa(ypb))
+            assert lo - 0.005 <= ratio <= hi, (re_tau, n, ratio)
+
+
+def test_cai_degrigny_wall_runs_and_is_beta_one_limit():
+    """The Cai-Degrigny wall is the HRFD wall with beta = 1 and Eq. 15 replaced by
+    Eq. 29 (Eq. 30): with the same velocity field its strain differs from HRFD
+    beta = 1 only through the ratio of the two derivatives."""
+    c = small_channel("wall_cai_degrigny", "D2Q9")
+    o = make(c)
+    o.run(20)
+    assert np.isfinite(o.fs).all()
+    assert np.all(o.utau["ymin"] > 0)
