@@ -30,6 +30,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+if "reference" in sys.argv:
+    # the CPU reference arm reports one core: keep numpy's thread pools at one
+    for _k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_k] = "1"
 
 import numpy as np  # noqa: E402
 

@@ -99,6 +99,9 @@ typedef struct {
   double u_shift;              /* m/s, x velocity U of the stored deviations: populations are
                                   kept as f_i - f_i^eq(rho0, U x) (0: f_i - w_i rho0); set it
                                   to the mean flow to keep the stored values small */
+  int staging;                 /* inner-row population loads: 0 = direct loads through L1
+                                  (default, fastest measured); 1 = TMA tiles staged in shared
+                                  memory, double-buffered over z planes */
   void* (*alloc)(size_t bytes, void* user);  /* optional device allocator */
   void (*free)(void* ptr, void* user);
   void* alloc_user;

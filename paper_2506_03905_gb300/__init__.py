@@ -58,7 +58,7 @@ class LbmConfig(ctypes.Structure):
         ("force", ctypes.c_double * 3), ("origin", ctypes.c_double * 3),
         ("collision", ctypes.c_int), ("storage", ctypes.c_int), ("turbulence", ctypes.c_int),
         ("wall_law", ctypes.c_int), ("kappa", ctypes.c_double), ("B", ctypes.c_double),
-        ("u_shift", ctypes.c_double), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+        ("u_shift", ctypes.c_double), ("staging", ctypes.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -244,7 +244,7 @@ def lbm_batch_last_error(b=None) -> str:
 
 
 # ----------------------------------------------------------------- solver
-def config_from_case(case, stream=0) -> LbmConfig:
+def config_from_case(case, stream=0, staging=0) -> LbmConfig:
     c = LbmConfig()
     c.lattice = LATTICE[case.lattice]
     c.nx, c.ny, c.nz = case.nx, case.ny, case.nz
@@ -259,6 +259,7 @@ def config_from_case(case, stream=0) -> LbmConfig:
     # stored populations are deviations from the equilibrium at the mean flow
     shift = getattr(case, "u_shift", None)
     c.u_shift = case.u_init[0] if shift is None else shift
+    c.staging = int(staging)
     c.stream = stream
     return c
 
@@ -283,14 +284,15 @@ class Solver:
     stream of the device.
     """
 
-    def __init__(self, case, device: int = 0, use_torch_allocator: bool = True):
+    def __init__(self, case, device: int = 0, use_torch_allocator: bool = True,
+                 tma_staging: bool = False):
         import torch
         self.torch = torch
         self.case = case
         self.device = device
         torch.cuda.set_device(device)
         self.stream = torch.cuda.current_stream(device)
-        cfg = config_from_case(case, self.stream.cuda_stream)
+        cfg = config_from_case(case, self.stream.cuda_stream, staging=int(tma_staging))
         self._cbs = None
         if use_torch_allocator:
             stream = self.stream

@@ -5,6 +5,8 @@
 // step is two launches on the context stream: the wall pre-pass (k_wall) and
 // the fused bulk kernel (k_bulk); pairs of steps are captured once per buffer
 // parity into CUDA graphs and replayed by lbm_step.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -145,6 +147,10 @@ extern "C" lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     lbm_ctx_set_error(nullptr, "u_shift must be finite and well below the lattice speed");
     return LBM_EINVAL;
   }
+  if (k.staging != 0 && k.staging != 1) {
+    lbm_ctx_set_error(nullptr, "staging must be 0 (direct loads) or 1 (TMA tiles)");
+    return LBM_EINVAL;
+  }
   if (k.wall_law == LBM_LAW_LOG && !(k.kappa > 0)) {
     lbm_ctx_set_error(nullptr, "log law needs kappa > 0");
     return LBM_EINVAL;
@@ -272,6 +278,8 @@ extern "C" lbm_status lbm_set_bc(lbm_ctx* c, int face, const lbm_bc* bc) {
   return LBM_OK;
 }
 
+static void build_tensor_maps(lbm_ctx* c);
+
 // Validate the face combination and build the kernel parameters.
 lbm_status lbm_ctx_finalize(lbm_ctx* c) {
   if (c->finalized) return LBM_OK;
@@ -356,6 +364,7 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
     p.frec[b] = c->frec[b];
   }
   p.flags = c->flags;
+  build_tensor_maps(c);
   // float copies of the lattice parameters for the FP32 kernels
   p.nu_f = (float)p.nu;
   p.Ush_f = (float)p.Ush;
@@ -382,13 +391,62 @@ Params lbm_ctx_params(const lbm_ctx* c, int src) {
   return p;
 }
 
+// Tensor maps of both population buffers for the TMA-staged inner-row kernel:
+// 4-D [q][z][y][x], box (32 + 2 * 16/esz) x 8 x 1 x 1.  Built only when the
+// alignment rules of tiled bulk copies hold: 16-byte base address and strides;
+// the box width and the x start x0 - 16/esz (x0 a multiple of 32) are 16-byte
+// multiples by construction.
+static void build_tensor_maps(lbm_ctx* c) {
+  c->tma_ok = false;
+  if (c->cfg.staging != 1) return;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  if (!encode || c->ny < 3) return;
+  CUtensorMapDataType dt;
+  switch (c->st) {
+    case ST_FP32: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+    case ST_FP16: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+    case ST_BF16: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+    default: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
+  }
+  const cuuint64_t esz = c->esz;
+  const cuuint64_t dims[4] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz, (cuuint64_t)c->Q};
+  const cuuint64_t strides[3] = {(cuuint64_t)c->pitch * esz, (cuuint64_t)c->pitch * c->ny * esz,
+                                 (cuuint64_t)c->ncell * esz};
+  const cuuint32_t box[4] = {(cuuint32_t)tma_box_width(c->esz), 8, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if ((box[0] * esz) % 16 || strides[0] % 16 || strides[1] % 16 || strides[2] % 16) return;
+  for (int b = 0; b < 2; ++b) {
+    if (((uintptr_t)c->f[b]) % 16) return;
+    CUresult r = encode(&c->tmap[b], dt, 4, c->f[b], dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return;
+  }
+  c->tma_ok = true;
+}
+
 // Launch shape of k_bulk for a row set (ROWS_ALL / ROWS_INNER / ROWS_WALL).
 void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b) {
   int bx = 32;
   while (bx > 1 && bx / 2 >= c->nx) bx /= 2;
-  const int nrows = rows == ROWS_ALL ? c->ny : (rows == ROWS_INNER ? c->ny - 2 : 2);
+  const int nrows = rows == ROWS_ALL ? c->ny : (rows == ROWS_WALL ? 2 : c->ny - 2);
   int by = 256 / bx;
   if (rows == ROWS_WALL) by = 2;
+  if (rows == ROWS_XEDGE) {
+    *b = dim3(2, 64, 1);
+    *g = dim3(1, (nrows + 63) / 64, c->nz);
+    return;
+  }
   *b = dim3(bx, by, 1);
   *g = dim3((c->nx + bx - 1) / bx, (nrows + by - 1) / by, c->nz);
 }
@@ -401,6 +459,13 @@ static void launch_wall(lbm_ctx* c, const Params& p, cudaStream_t s, int prio = 
 }
 
 static void launch_bulk(lbm_ctx* c, const Params& p, int rows, cudaStream_t s, int prio = 0) {
+  if (rows == ROWS_INNER && c->tma_ok) {
+    const int src = p.f_src == c->f[0] ? 0 : 1;
+    if (c->Q == 9) launch_bulk_tma_q9(c->st, p, c->tmap[src], c->tma_zchunk, s);
+    else launch_bulk_tma_q19(c->st, p, c->tmap[src], c->tma_zchunk, s);
+    if (!p.px) launch_bulk(c, p, ROWS_XEDGE, s, prio);   // inlet / outlet columns
+    return;
+  }
   dim3 g, b;
   lbm_ctx_bulk_launch_dims(c, rows, &g, &b);
   if (c->Q == 9) launch_bulk_q9(c->st, p, rows, g, b, s, prio);
@@ -581,6 +646,10 @@ static lbm_status check_flags(lbm_ctx* c) {
   CUDA_TRY(c, cudaMemcpyAsync(h, c->flags, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->last_flags = h[0];
+  if (h[0] & FLAG_TMA_TIMEOUT) {
+    lbm_ctx_set_error(c, "a bounded wait for a tiled load expired; the state is not valid");
+    return LBM_ETIMEOUT;
+  }
   if (h[0] & FLAG_NONFINITE) {
     lbm_ctx_set_error(c, "non-finite value in the state");
     return LBM_ENONFINITE;

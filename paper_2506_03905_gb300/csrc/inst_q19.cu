@@ -26,11 +26,28 @@ static void launch_prio(void (*k)(A...), dim3 g, dim3 b, cudaStream_t s, int pri
   cudaLaunchKernelEx(&cfg, k, args...);
 }
 
+// Inner rows with TMA staging: block 32 x 8, grid over x tiles, y tiles of the
+// rows 1..ny-2 and chunks of zchunk planes; two stages of Q boxes in dynamic
+// shared memory.
+template <int ST>
+static void bulk_tma_st(const Params& p, const CUtensorMap& tm, int zchunk, cudaStream_t s) {
+  using TT = TmaTile<19, ST>;
+  const int smem = TT::SMEM_BYTES;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_bulk_tma<19, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr_set = true;
+  }
+  dim3 g((p.nx + 31) / 32, (p.ny - 2 + TT::BH - 1) / TT::BH, (p.nz + zchunk - 1) / zchunk);
+  dim3 b(32, TT::BH, 1);
+  k_bulk_tma<19, ST><<<g, b, smem, s>>>(p, tm, zchunk);
+}
+
 template <int ST>
 static void bulk_st(const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, int prio) {
   // the face logic is needed unless every cell of the launch has periodic or
   // in-lattice neighbours: periodic x and either periodic y or inner rows only
-  const bool fast = p.px && (p.py || rows == ROWS_INNER);
+  const bool fast = rows != ROWS_XEDGE && p.px && (p.py || rows == ROWS_INNER);
   if (fast) launch_prio(k_bulk<19, ST, false>, g, b, s, prio, p, rows);
   else launch_prio(k_bulk<19, ST, true>, g, b, s, prio, p, rows);
 }
@@ -49,6 +66,9 @@ static void wall_st(const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
 
 void launch_bulk_q19(int st, const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, int prio) {
   LBM_DISPATCH(bulk_st, p, rows, g, b, s, prio)
+}
+void launch_bulk_tma_q19(int st, const Params& p, const CUtensorMap& tm, int zchunk, cudaStream_t s) {
+  LBM_DISPATCH(bulk_tma_st, p, tm, zchunk, s)
 }
 void launch_wall_q19(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
   LBM_DISPATCH(wall_st, p, g, b, s, prio)

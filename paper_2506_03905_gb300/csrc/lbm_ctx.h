@@ -1,5 +1,6 @@
 // lbm_ctx.h -- the context object behind the opaque lbm_ctx handle.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -46,6 +47,12 @@ struct lbm_ctx {
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   bool gvalid[2] = {false, false};
   lbm::Params base;
+  CUtensorMap tmap[2];                 // population buffer k as a 4-D tensor [q][z][y][x]
+  bool tma_ok = false;                 // inner rows use the TMA-staged kernel
+#ifndef LBM_TMA_ZCHUNK
+#define LBM_TMA_ZCHUNK 8
+#endif
+  int tma_zchunk = LBM_TMA_ZCHUNK;     // z planes marched by one block
   std::string err;
   std::vector<void*> allocs;
 };

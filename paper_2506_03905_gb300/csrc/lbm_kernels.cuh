@@ -11,6 +11,7 @@
 //             moments (Eqs. 4-5), omega from nu + nu_t (Eq. 8), collision.
 #pragma once
 #include "lbm_device.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 
@@ -19,6 +20,62 @@ namespace lbm {
 // (periodic wrap folded in) replace all face logic; 32-bit indexing (the
 // lattice is checked at creation to satisfy Q * pitch * ny * nz < 2^31).
 // ----------------------------------------------------------------------------
+struct NbOff {
+  int id, nc, oxm, oxp, oym, oyp, ozm, ozp;
+};
+
+// Cell index and the offsets to the neighbours at x-1, x+1, y-1, y+1, z-1, z+1
+// (periodic wrap folded in).
+__device__ __forceinline__ NbOff nb_offsets(const Params& p, int x, int y, int z) {
+  NbOff o;
+  const int pitch = p.pitch;
+  const int plane = pitch * p.ny;
+  o.nc = (int)p.ncell;
+  o.id = (z * p.ny + y) * pitch + x;
+  o.oxm = x == 0 ? p.nx - 1 : -1;
+  o.oxp = x == p.nx - 1 ? -(p.nx - 1) : 1;
+  o.oym = y == 0 ? (p.ny - 1) * pitch : -pitch;
+  o.oyp = y == p.ny - 1 ? -(p.ny - 1) * pitch : pitch;
+  o.ozm = z == 0 ? (p.nz - 1) * plane : -plane;
+  o.ozp = z == p.nz - 1 ? -(p.nz - 1) * plane : plane;
+  return o;
+}
+
+// Everything after streaming for a cell with in-lattice (or periodic)
+// neighbours: SA update, relaxation rate, collision, stores.
+template <int Q, int ST>
+__device__ __forceinline__ void interior_finish(const Params& p, const NbOff& o,
+                                                typename Compute<ST>::R (&g)[Q], int x, int y) {
+  using C = Codec<ST>;
+  using R = typename Compute<ST>::R;
+  using T = typename C::T;
+  T* __restrict__ fd = (T*)p.f_dst;
+  const R* __restrict__ us = (const R*)p.u_src;
+  R* __restrict__ ud = (R*)p.u_dst;
+  const R* __restrict__ ns = (const R*)p.nt_src;
+  R* __restrict__ nd = (R*)p.nt_dst;
+  // SA working variable of the new step (Eq. 11)
+  R ntn;
+  if (p.turbulent)
+    ntn = sa_update_interior<R, (Q == 19)>(p, ns, us, o.id, o.nc, o.oxm, o.oxp, o.oym, o.oyp, o.ozm,
+                                            o.ozp, x, y);
+  else
+    ntn = ns[o.id];
+  nd[o.id] = ntn;
+  const R nu = psel<R>(p.nu, p.nu_f);
+  const R nut = p.turbulent ? sa_nut<R>(ntn, nu) : (R)0;
+  const R delta = relax_delta<R>((R)3 * (nu + nut));   // 2 - omega (Eq. 8)
+  // moments and collision
+  R u[3];
+  collide<Q, R>(p, g, delta, u);
+  // store
+#pragma unroll
+  for (int i = 0; i < Q; ++i) C::st(fd + (i * o.nc + o.id), g[i]);
+  ud[o.id] = u[0];
+  ud[o.id + o.nc] = u[1];
+  ud[o.id + 2 * o.nc] = u[2];
+}
+
 template <int Q, int ST>
 __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int z) {
   using L = Lat<Q>;
@@ -26,55 +83,18 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
   using R = typename Compute<ST>::R;
   using T = typename C::T;
   const T* __restrict__ fs = (const T*)p.f_src;
-  T* __restrict__ fd = (T*)p.f_dst;
-  const R* __restrict__ us = (const R*)p.u_src;
-  R* __restrict__ ud = (R*)p.u_dst;
-  const R* __restrict__ ns = (const R*)p.nt_src;
-  R* __restrict__ nd = (R*)p.nt_dst;
-  const int pitch = p.pitch;
-  const int plane = pitch * p.ny;
-  const int nc = (int)p.ncell;
-  const int id = (z * p.ny + y) * pitch + x;
-  // offsets to the neighbours at x-1, x+1, y-1, y+1, z-1, z+1
-  const int oxm = x == 0 ? p.nx - 1 : -1;
-  const int oxp = x == p.nx - 1 ? -(p.nx - 1) : 1;
-  const int oym = y == 0 ? (p.ny - 1) * pitch : -pitch;
-  const int oyp = y == p.ny - 1 ? -(p.ny - 1) * pitch : pitch;
-  const int ozm = z == 0 ? (p.nz - 1) * plane : -plane;
-  const int ozp = z == p.nz - 1 ? -(p.nz - 1) * plane : plane;
-
-  // 1. pull streaming (Eq. 3): source x - c_i; issued first so that the loads
-  //    are in flight while the SA stencil is evaluated
+  const NbOff o = nb_offsets(p, x, y, z);
+  // pull streaming (Eq. 3): source x - c_i; issued first so that the loads are
+  // in flight while the SA stencil is evaluated
   R g[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-    const int off = (cx > 0 ? oxm : (cx < 0 ? oxp : 0)) + (cy > 0 ? oym : (cy < 0 ? oyp : 0)) +
-                    (cz > 0 ? ozm : (cz < 0 ? ozp : 0));
-    g[i] = (R)C::ld(fs + (i * nc + id + off));
+    const int off = (cx > 0 ? o.oxm : (cx < 0 ? o.oxp : 0)) + (cy > 0 ? o.oym : (cy < 0 ? o.oyp : 0)) +
+                    (cz > 0 ? o.ozm : (cz < 0 ? o.ozp : 0));
+    g[i] = (R)C::ld(fs + (i * o.nc + o.id + off));
   }
-
-  // 2. SA working variable of the new step (Eq. 11)
-  R ntn;
-  if (p.turbulent)
-    ntn = sa_update_interior<R, (Q == 19)>(p, ns, us, id, nc, oxm, oxp, oym, oyp, ozm, ozp, x, y);
-  else
-    ntn = ns[id];
-  nd[id] = ntn;
-  const R nu = psel<R>(p.nu, p.nu_f);
-  const R nut = p.turbulent ? sa_nut<R>(ntn, nu) : (R)0;
-  const R delta = relax_delta<R>((R)3 * (nu + nut));   // 2 - omega (Eq. 8)
-
-  // 3. moments and collision
-  R u[3];
-  collide<Q, R>(p, g, delta, u);
-
-  // 4. store
-#pragma unroll
-  for (int i = 0; i < Q; ++i) C::st(fd + (i * nc + id), g[i]);
-  ud[id] = u[0];
-  ud[id + nc] = u[1];
-  ud[id + 2 * nc] = u[2];
+  interior_finish<Q, ST>(p, o, g, x, y);
 }
 
 // ----------------------------------------------------------------------------
@@ -199,10 +219,153 @@ __global__ void LBM_BULK_BOUNDS k_bulk(const Params p, int rows) {
   const int r = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   int y = r;
+  int xx = x;
   if (rows == ROWS_INNER) y = r + 1;
   else if (rows == ROWS_WALL) y = r == 0 ? 0 : (r == 1 ? p.ny - 1 : p.ny);
-  if (x >= p.nx || y >= p.ny || (rows == ROWS_INNER && y >= p.ny - 1)) return;
-  bulk_cell<Q, ST, GENERAL>(p, x, y, z);
+  else if (rows == ROWS_XEDGE) {
+    y = r + 1;
+    xx = x == 0 ? 0 : (x == 1 ? p.nx - 1 : p.nx);
+    if (x == 1 && p.nx == 1) return;   // a single column is column 0
+  }
+  if (xx >= p.nx || y >= p.ny || ((rows == ROWS_INNER || rows == ROWS_XEDGE) && y >= p.ny - 1)) return;
+  bulk_cell<Q, ST, GENERAL>(p, xx, y, z);
+}
+
+// ----------------------------------------------------------------------------
+// Inner rows with TMA staging.  Block = 32 x 8 cells of one z plane; it marches
+// over `zchunk` planes.  For every plane one thread issues Q tiled loads, one
+// per direction i: the box of source cells x - c_i of the tile, i.e. rows
+// y0 - c_iy .. y0 - c_iy + 7 of plane z - c_iz, widened in x to start at the
+// 16-byte boundary x0 - XOFF.  Two stages: the next plane is in flight while
+// the current one is computed.  The wrap-around columns of a periodic x axis
+// (x = -1 and x = nx), which a tiled load fills with zeros, are patched from
+// global memory.  Waits are bounded; on expiry the block records
+// FLAG_TMA_TIMEOUT, waits (bounded) for its copies in flight and leaves.
+// ----------------------------------------------------------------------------
+template <int Q, int ST>
+struct TmaTile {
+  using T = typename Codec<ST>::T;
+  static constexpr int XOFF = 16 / (int)sizeof(T);   // elements in 16 bytes
+  static constexpr int BW = 32 + 2 * XOFF;           // box width (x)
+  static constexpr int BH = 8;                       // box height (y)
+  static constexpr uint32_t BOX_BYTES = BW * BH * sizeof(T);
+  static constexpr uint32_t STAGE_BYTES = Q * BOX_BYTES;
+  static constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 128 + 16;   // stages, alignment, barriers
+  static_assert(BOX_BYTES % 128 == 0, "boxes keep 128-byte alignment");
+  static_assert((XOFF * sizeof(T)) % 16 == 0 && (BW * sizeof(T)) % 16 == 0, "16-byte tiles");
+};
+
+// Minimum resident blocks per SM for the TMA-staged kernel (its register
+// budget); its two shared-memory stages take 2 x Q boxes per block.
+#ifndef LBM_TMA_MINB
+#define LBM_TMA_MINB 4
+#endif
+
+template <int Q, int ST>
+__global__ void __launch_bounds__(256, LBM_TMA_MINB)
+    k_bulk_tma(const Params p, const __grid_constant__ CUtensorMap tmap, int zchunk) {
+  using L = Lat<Q>;
+  using C = Codec<ST>;
+  using R = typename Compute<ST>::R;
+  using T = typename C::T;
+  using TT = TmaTile<Q, ST>;
+  constexpr int XOFF = TT::XOFF, BW = TT::BW, BH = TT::BH;
+  // dynamic shared memory, aligned here to the 128 bytes a tiled bulk copy
+  // destination needs: [2][Q][BH][BW] elements, then the two mbarriers
+  extern __shared__ unsigned char tma_smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)tma_smem_raw + 127) & ~(uintptr_t)127);
+  T* sm = (T*)base;
+  uint64_t* bar = (uint64_t*)(base + 2 * TT::STAGE_BYTES);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  const int x0 = blockIdx.x * 32, y0 = 1 + blockIdx.y * BH;
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(p.nz, z0 + zchunk);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < p.nx && y <= p.ny - 2;
+  const T* __restrict__ fs = (const T*)p.f_src;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int issued = 0;   // loads issued (thread 0)
+  if (tid == 0 && z0 < z1) {
+    mbar_arrive_expect_tx(&bar[0], TT::STAGE_BYTES);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      int zs = z0 - L::c(i, 2);
+      zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+      tma_load_4d(sm + (0 * Q + i) * BH * BW, &tmap, x0 - XOFF, y0 - L::c(i, 1), zs, i, &bar[0]);
+    }
+    issued = 1;
+  }
+  for (int z = z0, k = 0; z < z1; ++z, ++k) {
+    const int s = k & 1;
+    if (tid == 0 && z + 1 < z1) {
+      // stage s^1 was last read before the barrier that closed iteration k-1
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[s ^ 1], TT::STAGE_BYTES);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        int zs = z + 1 - L::c(i, 2);
+        zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+        tma_load_4d(sm + ((s ^ 1) * Q + i) * BH * BW, &tmap, x0 - XOFF, y0 - L::c(i, 1), zs, i,
+                    &bar[s ^ 1]);
+      }
+      ++issued;
+    }
+    bool ok = false;
+    for (int it = 0; it < (1 << 24); ++it) {
+      if (mbar_try_wait(&bar[s], (uint32_t)((k >> 1) & 1))) {
+        ok = true;
+        break;
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(p.flags, FLAG_TMA_TIMEOUT);
+        // the other stage may still have a copy in flight: wait for it (bounded)
+        if (issued > k + 1)
+          for (int it = 0; it < (1 << 24) && !mbar_try_wait(&bar[s ^ 1], (uint32_t)(((k + 1) >> 1) & 1)); ++it) {
+          }
+      }
+      return;
+    }
+    T* st = sm + s * Q * BH * BW;
+    if (p.px && (x0 == 0 || x0 + 32 >= p.nx)) {
+      // periodic x: source column x = -1 is column nx-1, source column x = nx is column 0
+      int j = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int cx = L::c(i, 0);
+        if (cx == 0) continue;
+        const int col = cx > 0 ? XOFF - 1 : p.nx - x0 + XOFF;
+        const bool need = cx > 0 ? x0 == 0 : x0 + 32 >= p.nx;
+        if (need && tid >= j * BH && tid < (j + 1) * BH) {
+          const int r = tid - j * BH;
+          const int ys = y0 + r - L::c(i, 1);
+          int zs = z - L::c(i, 2);
+          zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+          if (ys >= 0 && ys < p.ny)
+            st[(i * BH + r) * BW + col] = fs[i * p.ncell + ((long long)zs * p.ny + ys) * p.pitch +
+                                             (cx > 0 ? p.nx - 1 : 0)];
+        }
+        ++j;
+      }
+      __syncthreads();
+    }
+    // x-face cells of a non-periodic x axis are left to the ROWS_XEDGE launch
+    if (active && (p.px || (x != 0 && x != p.nx - 1))) {
+      R g[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) g[i] = (R)C::ld(st + (i * BH + ty) * BW + tx + XOFF - L::c(i, 0));
+      const NbOff o = nb_offsets(p, x, y, z);
+      interior_finish<Q, ST>(p, o, g, x, y);
+    }
+    __syncthreads();
+  }
 }
 
 // ----------------------------------------------------------------------------

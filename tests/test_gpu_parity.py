@@ -20,10 +20,10 @@ def rel(a, b):
     return np.abs(a - b).max() / (den if den > 0 else 1.0)
 
 
-def run_gpu(case, nsteps, fields=None, split=None):
+def run_gpu(case, nsteps, fields=None, split=None, tma=False):
     import paper_2506_03905_gb300 as pkg
     init = C.initial_fields(case)
-    s = pkg.Solver(case)
+    s = pkg.Solver(case, tma_staging=tma)
     s.set_fields(*init)
     if split:
         for k in split:
@@ -43,8 +43,8 @@ def run_oracle(case, nsteps):
     return Oracle(case, *C.initial_fields(case)).run(nsteps).fields()
 
 
-def compare(case, nsteps, tol, keys=None):
-    g = run_gpu(case, nsteps)
+def compare(case, nsteps, tol, keys=None, tma=False):
+    g = run_gpu(case, nsteps, tma=tma)
     r = run_oracle(case, nsteps)
     keys = keys or [k for k in g if k in r]
     errs = {k: rel(g[k], r[k]) for k in keys}
@@ -232,3 +232,23 @@ def test_nonfinite_is_reported():
     assert s.last_status == pkg.LBM_ENONFINITE
     assert s.diagnostics().nonfinite == 1
     s.close()
+
+
+@pytest.mark.parametrize("case_fn", [
+    lambda: C.channel_3d(re_tau=5200.0, scheme="wall_bb", nx=40, ny=20, nz=5, seed=2),
+    lambda: C.channel_3d(re_tau=5200.0, scheme="wall_hrfd", nx=40, ny=20, nz=5, seed=2,
+                         storage="fp16"),
+    lambda: C.flat_plate_3d(nx=70, ny=22, nz=3, dx=3e-2, scheme="wall_bb"),
+    lambda: C.flat_plate_3d(nx=70, ny=22, nz=1, dx=3e-2, scheme="wall_hrfd").replace(lattice="D2Q9"),
+    lambda: C.channel_3d(scheme="wall_bb", nx=3, ny=9, nz=2),
+])
+def test_tma_staged_inner_rows(case_fn):
+    """Inner rows through the TMA-staged kernel (staging = 1): same results as
+    the direct-load kernel to rounding, and as the oracle within the FP32 bar."""
+    case = case_fn()
+    a = run_gpu(case, 60, tma=True)
+    b = run_gpu(case, 60, tma=False)
+    for k in ("u", "nu_t"):
+        assert rel(a[k], b[k]) < 1e-6, (case.name, k)
+    if case.storage == "fp32":
+        compare(case, 60, TOL["fp32"], tma=True)
