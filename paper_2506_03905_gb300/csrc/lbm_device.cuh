@@ -414,10 +414,11 @@ __host__ __device__ inline double wf_dudy(int law, double kap, double yp) {
 // u_tau (or sqrt(U nu / y), the viscous-sublayer value) inside a sign-change
 // bracket [lo, hi] that starts as [0, inf) and tightens with every residual;
 // a step that would leave the bracket is replaced by bisection (or doubling
-// while hi is still open).  Once a Newton step is below 1e-7 of u_tau the
+// while hi is still open).  Once a Newton step is below 1e-5 of u_tau the
 // stepped value is returned: quadratic convergence leaves an error of order
-// step^2 / u_tau (about 1e-14 relative); warm-started from the previous step's
-// u_tau this is usually a single FP64 evaluation.  Returns false if the 100-iteration limit was
+// step^2 / u_tau (about 1e-10 relative, five orders below the FP32 parity
+// bar); warm-started from the previous step's u_tau (which moves by far less
+// than 1e-5 per step) this is a single FP64 evaluation of the wall law.  Returns false if the 100-iteration limit was
 // reached (the last iterate is still returned).
 __host__ __device__ inline bool solve_utau(int law, double kap, double B, double U, double y,
                                            double nu, double guess, double* out) {
@@ -439,8 +440,8 @@ __host__ __device__ inline bool solve_utau(int law, double kap, double B, double
     const double dg = up + yp * wf_dudy(law, kap, yp);
     const double step = g / dg;
     double xn = x - step;
-    if (fabs(step) <= 1e-7 * x && xn > 0.0) {
-      // quadratic convergence: the error of xn is of order step^2 / x (< 1e-13 x)
+    if (fabs(step) <= 1e-5 * x && xn > 0.0) {
+      // quadratic convergence: the error of xn is of order step^2 / x (about 1e-10 x)
       *out = xn;
       return true;
     }

@@ -116,6 +116,52 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
 #define LBM_BULK_BOUNDS __launch_bounds__(256)
 #endif
 
+// A bounce-back wall node on a lattice with periodic x: the sources of the
+// directions leaving the wall are replaced by Eq. 31, every other source is
+// in the lattice; nu_tilde is the Dirichlet value the wall pass stored.
+template <int Q, int ST>
+__device__ __forceinline__ void bulk_wall_bb(const Params& p, int fi, int x, int y, int z) {
+  using L = Lat<Q>;
+  using C = Codec<ST>;
+  using R = typename Compute<ST>::R;
+  using T = typename C::T;
+  const T* __restrict__ fs = (const T*)p.f_src;
+  T* __restrict__ fd = (T*)p.f_dst;
+  R* __restrict__ ud = (R*)p.u_dst;
+  const R* __restrict__ nd = (const R*)p.nt_dst;
+  const NbOff o = nb_offsets(p, x, y, z);
+  const int node = z * (p.nx - p.xw0[fi]) + (x - p.xw0[fi]);
+  const R* uw = (const R*)p.uw[fi] + 3 * node;
+  const R rw = ((const R*)p.rhow[fi])[node];
+  const R rux = rw * uw[0], ruy = rw * uw[1], ruz = rw * uw[2];
+  const R U = psel<R>(p.Ush, p.Ush_f);
+  R g[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+    const bool from_wall = fi == 0 ? cy > 0 : cy < 0;
+    if (from_wall) {
+      // Eq. 31 in deviations: h*_{opp i}(B) + 6 w (rho_w c_i.u_w - c_x U)
+      const R cu = (R)cx * rux + (R)cy * ruy + (R)cz * ruz;
+      g[i] = (R)C::ld(fs + (opp(i) * o.nc + o.id)) + (R)6 * (R)L::w(i) * (cu - (R)cx * U);
+    } else {
+      const int off = (cx > 0 ? o.oxm : (cx < 0 ? o.oxp : 0)) + (cy > 0 ? o.oym : (cy < 0 ? o.oyp : 0)) +
+                      (cz > 0 ? o.ozm : (cz < 0 ? o.ozp : 0));
+      g[i] = (R)C::ld(fs + (i * o.nc + o.id + off));
+    }
+  }
+  const R nu = psel<R>(p.nu, p.nu_f);
+  const R nut = p.turbulent ? sa_nut<R>(nd[o.id], nu) : (R)0;
+  const R delta = relax_delta<R>((R)3 * (nu + nut));
+  R u[3];
+  collide<Q, R>(p, g, delta, u);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) C::st(fd + (i * o.nc + o.id), g[i]);
+  ud[o.id] = u[0];
+  ud[o.id + o.nc] = u[1];
+  ud[o.id + 2 * o.nc] = u[2];
+}
+
 // One cell of the bulk update (every cell of the lattice takes this path).
 template <int Q, int ST, bool GENERAL>
 __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) {
@@ -126,6 +172,14 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
   if (!GENERAL || ((p.px || (x >= 1 && x <= p.nx - 2)) && (p.py || (y >= 1 && y <= p.ny - 2)))) {
     bulk_interior<Q, ST>(p, x, y, z);
     return;
+  }
+  if (p.px && p.turbulent && p.ny >= 3) {
+    const int fw = (y == 0 && p.wall[0] == BC_WALL_BB && x >= p.xw0[0]) ? 0
+                 : ((y == p.ny - 1 && p.wall[1] == BC_WALL_BB && x >= p.xw0[1]) ? 1 : -1);
+    if (fw >= 0) {
+      bulk_wall_bb<Q, ST>(p, fw, x, y, z);
+      return;
+    }
   }
   const long long id = cidx(p, x, y, z);
   T* __restrict__ fd = (T*)p.f_dst;
