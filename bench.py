@@ -262,6 +262,17 @@ def run_ours(args):
                 "alg_bytes_per_cell": ALG_BYTES[(vc.lattice, vc.storage)],
                 "bulk_frac_of_hbm": round(vb / (vbulk * 1e-3) / 1e9 / peak, 4),
                 "nonfinite": int(vd.nonfinite)}
+        # the flat-plate workload at full size (2048 x 512 x 8, regularized collision)
+        for label, scheme in [("plate_fp32_bb", "wall_bb"), ("plate_fp32_hrfd", "wall_hrfd")]:
+            pc = C.flat_plate_3d(scheme=scheme)
+            pms, pbulk, pwall, pd = time_case(pkg, pc, vsteps, 3, torch)
+            pb = ALG_BYTES[(pc.lattice, pc.storage)] * pc.cells
+            variants[label] = {
+                "mlups": round(pc.cells * vsteps / (pms * 1e-3) / 1e6, 1),
+                "bulk_ms": round(pbulk, 4), "wall_ms": round(pwall, 4),
+                "alg_bytes_per_cell": ALG_BYTES[(pc.lattice, pc.storage)],
+                "bulk_frac_of_hbm": round(pb / (pbulk * 1e-3) / 1e9 / peak, 4),
+                "nonfinite": int(pd.nonfinite)}
         try:
             variants.update(batched_variant(pkg, torch, vsteps))
         except Exception as exc:  # the batched path reports its own status
