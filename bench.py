@@ -203,9 +203,11 @@ def run_ours(args):
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    n_launch0 = s.kernel_launches()
     e0.record(s.stream)
     s.step(args.steps)
     e1.record(s.stream)
+    n_launches = s.kernel_launches() - n_launch0
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
@@ -296,7 +298,7 @@ def run_ours(args):
                      "bulk_ms": round(bulk_avg, 4), "wall_pass_ms": round(wall_ms / args.steps, 4)},
         "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "status": int(st)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": int(n_launches),
         "clocks": clk,
         "diagnostics": {"mass": diag.mass, "nonfinite": int(diag.nonfinite),
                         "mean_u_tau": list(diag.mean_u_tau)},

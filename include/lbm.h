@@ -181,6 +181,13 @@ void lbm_destroy(lbm_ctx* ctx);
 /* Message of the last failure of this context (static storage if ctx is NULL). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 
+/* Number of kernels this context has put on the GPU since lbm_create: every
+   launch of lbm_set_fields, lbm_step (the kernels of replayed graphs
+   included), lbm_step_timed, lbm_fields and lbm_diagnostics.  A host-side
+   count that never synchronises; 0 for NULL.  Bookkeeping for benchmarks: the
+   paper has no counterpart. */
+unsigned long long lbm_kernel_launches(const lbm_ctx* ctx);
+
 /* Lattice parameters after unit conversion: out[0] = dt (s), out[1] = nu
    (lattice), out[2] = tau0, out[3..5] = F (lattice). */
 lbm_status lbm_lattice_params(const lbm_ctx* ctx, double out[6]);

@@ -26,6 +26,7 @@ __all__ = [
     "lbm_diagnostics", "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_destroy",
     "lbm_last_error", "lbm_lattice_params", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tune", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_moments_noalloc",
+    "lbm_kernel_launches",
 ]
 
 LIB_PATH = _build.LIB
@@ -113,6 +114,7 @@ def lib():
         "lbm_set_state": (ctypes.c_int, [_P, _P]),
         "lbm_destroy": (None, [_P]),
         "lbm_last_error": (ctypes.c_char_p, [_P]),
+        "lbm_kernel_launches": (ctypes.c_ulonglong, [_P]),
         "lbm_lattice_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
         "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
         "lbm_batch_step": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -197,6 +199,10 @@ def lbm_destroy(ctx):
 def lbm_last_error(ctx=None) -> str:
     s = lib().lbm_last_error(ctx)
     return s.decode() if s else ""
+
+
+def lbm_kernel_launches(ctx) -> int:
+    return int(lib().lbm_kernel_launches(ctx))
 
 
 def lbm_lattice_params(ctx):
@@ -371,6 +377,9 @@ class Solver:
 
     def lattice_params(self):
         return lbm_lattice_params(self.ctx)
+
+    def kernel_launches(self) -> int:
+        return lbm_kernel_launches(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

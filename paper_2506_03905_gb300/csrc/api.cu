@@ -3,8 +3,11 @@
 // A context owns the double-buffered population, velocity and nu_tilde fields,
 // the per-wall-node state of both y faces and the FP64 reduction scratch.  A
 // step is two launches on the context stream: the wall pre-pass (k_wall) and
-// the fused bulk kernel (k_bulk); pairs of steps are captured once per buffer
-// parity into CUDA graphs and replayed by lbm_step.
+// the fused bulk kernel (k_bulk).  With walls a step is three launches issued
+// directly: the wall pre-pass and then the two wall rows on a high-priority
+// side stream, the inner rows on the context stream.  Without walls a step is
+// one bulk launch, and pairs of steps are captured once per buffer parity into
+// CUDA graphs and replayed by lbm_step.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -456,6 +459,7 @@ static void launch_wall(lbm_ctx* c, const Params& p, cudaStream_t s, int prio = 
   dim3 g((maxw + 127) / 128, 2, 1), b(128, 1, 1);
   if (c->Q == 9) launch_wall_q9(c->st, p, g, b, s, prio);
   else launch_wall_q19(c->st, p, g, b, s, prio);
+  ++c->launches;
 }
 
 static void launch_bulk(lbm_ctx* c, const Params& p, int rows, cudaStream_t s, int prio = 0) {
@@ -463,6 +467,7 @@ static void launch_bulk(lbm_ctx* c, const Params& p, int rows, cudaStream_t s, i
     const int src = p.f_src == c->f[0] ? 0 : 1;
     if (c->Q == 9) launch_bulk_tma_q9(c->st, p, c->tmap[src], c->tma_zchunk, s);
     else launch_bulk_tma_q19(c->st, p, c->tmap[src], c->tma_zchunk, s);
+    ++c->launches;
     if (!p.px) launch_bulk(c, p, ROWS_XEDGE, s, prio);   // inlet / outlet columns
     return;
   }
@@ -470,6 +475,20 @@ static void launch_bulk(lbm_ctx* c, const Params& p, int rows, cudaStream_t s, i
   lbm_ctx_bulk_launch_dims(c, rows, &g, &b);
   if (c->Q == 9) launch_bulk_q9(c->st, p, rows, g, b, s, prio);
   else launch_bulk_q19(c->st, p, rows, g, b, s, prio);
+  ++c->launches;
+  if (rows == ROWS_INNER && !p.px) launch_bulk(c, p, ROWS_XEDGE, s, prio);   // inlet / outlet columns
+}
+
+// Every row of a lattice without walls.  Periodic in x and y: one launch of
+// the face-free kernel; otherwise the inner rows take the face-free kernel and
+// only the face rows and columns the general one.
+static void launch_all_rows(lbm_ctx* c, const Params& p, cudaStream_t s) {
+  if ((p.px && p.py) || c->ny < 3) {
+    launch_bulk(c, p, ROWS_ALL, s);
+    return;
+  }
+  launch_bulk(c, p, ROWS_INNER, s);
+  launch_bulk(c, p, ROWS_WALL, s);
 }
 
 // One step.  With walls, only the two wall rows depend on the wall pre-pass:
@@ -478,7 +497,7 @@ static void launch_bulk(lbm_ctx* c, const Params& p, int rows, cudaStream_t s, i
 static void launch_step(lbm_ctx* c, int src, cudaStream_t s) {
   const Params p = lbm_ctx_params(c, src);
   if (!(p.wall[0] || p.wall[1])) {
-    launch_bulk(c, p, ROWS_ALL, s);
+    launch_all_rows(c, p, s);
     return;
   }
   cudaEventRecord(c->ev_fork, s);
@@ -524,6 +543,7 @@ extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double
     launch_init_q9(c->st, p, grid, drho, du, dnt, c->cfg.rho0, c->ucv, c->nucv, c->stream);
   else
     launch_init_q19(c->st, p, grid, drho, du, dnt, c->cfg.rho0, c->ucv, c->nucv, c->stream);
+  ++c->launches;
   for (int b = 0; b < 2; ++b)
     CUDA_TRY(c, cudaMemsetAsync(c->utau[b], 0, (size_t)c->nx * c->nz * sizeof(double), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->utau_prev, 0, 2 * (size_t)c->nx * c->nz * sizeof(double), c->stream));
@@ -541,8 +561,12 @@ static lbm_status ensure_graph(lbm_ctx* c, int parity) {
     c->gexec[parity] = nullptr;
   }
   CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  // kernels recorded into the graph are counted when it is replayed
+  const unsigned long long before = c->launches;
   launch_step(c, parity, c->cap_stream);
   launch_step(c, 1 - parity, c->cap_stream);
+  c->graph_launches[parity] = c->launches - before;
+  c->launches = before;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess) {
@@ -585,6 +609,7 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     if (s != LBM_OK) return s;
     while (left >= 2) {
       CUDA_TRY(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
+      c->launches += c->graph_launches[c->cur];
       left -= 2;
     }
   }
@@ -619,7 +644,7 @@ extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int nsteps, float kernel_ms[2])
       launch_bulk(c, p, ROWS_INNER, c->stream);
       launch_bulk(c, p, ROWS_WALL, c->stream);
     } else {
-      launch_bulk(c, p, ROWS_ALL, c->stream);
+      launch_all_rows(c, p, c->stream);
     }
     CUDA_TRY(c, cudaEventRecord(ev[3 * k + 2], c->stream));
     c->cur ^= 1;
@@ -693,6 +718,7 @@ extern "C" lbm_status lbm_fields(lbm_ctx* c, unsigned mask, void* const* dst, in
       launch_fields_q9(c->st, p, grid, a[0], a[1], a[2], a[3], c->cfg.rho0, vel, visc, c->stream);
     else
       launch_fields_q19(c->st, p, grid, a[0], a[1], a[2], a[3], c->cfg.rho0, vel, visc, c->stream);
+    ++c->launches;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && !dst_on_device)
       e = cudaMemcpyAsync(out, tmp, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -747,6 +773,7 @@ extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out) {
   else launch_reduce_q19(c->st, p, c->red_blocks, c->partial, c->red_chunk, c->stream);
   launch_reduce_final(c->partial, c->red_blocks, c->red_out, c->stream);
   launch_wall_stats(p, c->utau_prev, c->red_out + 8, c->stream);
+  c->launches += 3;
   CUDA_TRY(c, cudaGetLastError());
   double h[16];
   CUDA_TRY(c, cudaMemcpyAsync(h, c->red_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -833,4 +860,8 @@ extern "C" void lbm_destroy(lbm_ctx* c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
+}
+
+extern "C" unsigned long long lbm_kernel_launches(const lbm_ctx* c) {
+  return c ? c->launches : 0ULL;
 }

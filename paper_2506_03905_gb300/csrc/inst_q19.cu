@@ -46,8 +46,10 @@ static void bulk_tma_st(const Params& p, const CUtensorMap& tm, int zchunk, cuda
 template <int ST>
 static void bulk_st(const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, int prio) {
   // the face logic is needed unless every cell of the launch has periodic or
-  // in-lattice neighbours: periodic x and either periodic y or inner rows only
-  const bool fast = rows != ROWS_XEDGE && p.px && (p.py || rows == ROWS_INNER);
+  // in-lattice neighbours: the inner rows (whose x-face columns of a
+  // non-periodic x axis go to a separate ROWS_XEDGE launch), or every row of
+  // a lattice periodic in x and y
+  const bool fast = rows == ROWS_INNER || (rows == ROWS_ALL && p.px && p.py);
   if (fast) launch_prio(k_bulk<19, ST, false>, g, b, s, prio, p, rows);
   else launch_prio(k_bulk<19, ST, true>, g, b, s, prio, p, rows);
 }

@@ -44,6 +44,8 @@ struct lbm_ctx {
   bool ready = false;
   bool finalized = false;
   long long steps_done = 0;
+  unsigned long long launches = 0;   // kernels launched (graph replays included)
+  unsigned long long graph_launches[2] = {0, 0};   // kernels in each captured graph
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   bool gvalid[2] = {false, false};
   lbm::Params base;

@@ -27,9 +27,10 @@ enum { XMIN = 0, XMAX = 1, YMIN = 2, YMAX = 3 };
 enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2, ST_FP64 = 3 };
 enum { FLAG_NONFINITE = 1u, FLAG_NEWTON = 2u, FLAG_TMA_TIMEOUT = 4u };
 // k_bulk row sets: ROWS_ALL every row; ROWS_INNER rows 1..ny-2 (independent of
-// the wall pre-pass, so they run concurrently with it); ROWS_WALL rows 0, ny-1.
-// ROWS_XEDGE: columns 0 and nx-1 of rows 1..ny-2 (the x-face cells of a
-// non-periodic x axis, which the TMA-staged inner-row kernel leaves out).
+// the wall pre-pass, so they run concurrently with it) without the x-face
+// columns of a non-periodic x axis; ROWS_WALL rows 0, ny-1.  ROWS_XEDGE:
+// columns 0 and nx-1 of rows 1..ny-2 (the x-face cells of a non-periodic x
+// axis, which both inner-row kernels leave out).
 enum { ROWS_ALL = 0, ROWS_INNER = 1, ROWS_WALL = 2, ROWS_XEDGE = 3 };
 constexpr int RED_THREADS = 256;   // FP64 reduction block size
 constexpr int RED_VALS = 4;        // mass, momentum x/y/z

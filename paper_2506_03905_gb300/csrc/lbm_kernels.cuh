@@ -282,6 +282,8 @@ __global__ void LBM_BULK_BOUNDS k_bulk(const Params p, int rows) {
     if (x == 1 && p.nx == 1) return;   // a single column is column 0
   }
   if (xx >= p.nx || y >= p.ny || ((rows == ROWS_INNER || rows == ROWS_XEDGE) && y >= p.ny - 1)) return;
+  // x-face columns of a non-periodic x axis belong to the ROWS_XEDGE launch
+  if (rows == ROWS_INNER && !p.px && (xx == 0 || xx == p.nx - 1)) return;
   bulk_cell<Q, ST, GENERAL>(p, xx, y, z);
 }
 

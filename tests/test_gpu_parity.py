@@ -252,3 +252,23 @@ def test_tma_staged_inner_rows(case_fn):
         assert rel(a[k], b[k]) < 1e-6, (case.name, k)
     if case.storage == "fp32":
         compare(case, 60, TOL["fp32"], tma=True)
+
+
+def test_kernel_launch_count():
+    """Three launches per step with walls (wall pre-pass, wall rows, inner rows);
+    one per step without (graph replays counted by their recorded kernels)."""
+    import paper_2506_03905_gb300 as pkg
+    for scheme, per_step in [("wall_bb", 3), (None, 1)]:
+        case = C.channel_3d(scheme=scheme or "wall_bb", nx=24, ny=12, nz=3)
+        if scheme is None:
+            case = case.replace(bcs={"ymin": C.BC("periodic"), "ymax": C.BC("periodic")})
+        s = pkg.Solver(case)
+        s.set_fields(*C.initial_fields(case))
+        n0 = s.kernel_launches()
+        s.step(7)
+        n1 = s.kernel_launches()
+        s.step(4)
+        n2 = s.kernel_launches()
+        s.close()
+        assert n0 >= 1
+        assert (n1 - n0, n2 - n1) == (7 * per_step, 4 * per_step)
