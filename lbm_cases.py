@@ -32,6 +32,9 @@ import numpy as np
 FACES = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
 BC_KINDS = ("periodic", "wall_bb", "wall_hrfd", "symmetry", "inlet_zouhe",
             "outlet_zerograd", "freestream", "wall_cai_degrigny")
+# bounce-back variants for a wall that is not half-way between lattice nodes:
+# none (half-way, Eq. 31), Bouzidi (Eq. 36), Yu (Eq. 37)
+BB_INTERP = ("none", "bouzidi", "yu")
 
 NU_AIR = 1.5e-5          # m^2/s, Section 4.1.1 and Section 4.2.1
 RHO0 = 1.0               # kg/m^3, Section 4.1.1
@@ -49,10 +52,14 @@ class BC:
     x_start: float = -math.inf       # wall active where cell-centre x >= x_start
     u_in: Tuple[float, float, float] = (0.0, 0.0, 0.0)   # inlet / free-stream velocity
     nut_ratio_in: float = 3.0        # inlet / free-stream nu_tilde / nu
+    d_w: float = 0.5                 # wall-to-boundary-node distance / Delta (Section 4.1.2.5)
+    interp: str = "none"             # bounce-back walls: "none" | "bouzidi" | "yu"
 
     def __post_init__(self):
         if self.kind not in BC_KINDS:
             raise ValueError(f"unknown boundary kind {self.kind!r}")
+        if self.interp not in BB_INTERP:
+            raise ValueError(f"unknown bounce-back interpolation {self.interp!r}")
 
 
 @dataclass
@@ -167,17 +174,22 @@ def half_channel_2d(re_tau: float = 2000.0, ny: int = 48, nx: int = 4,
 def channel_3d(re_tau: float = 5200.0, scheme: str = "wall_bb", nx: int = 256,
                ny: int = 128, nz: int = 128, seed: int = 0, storage: str = "fp32",
                collision: str = "bgk", wall_law: str = "sa_analytic",
-               ref_node: int = 2, steps: int = 1000) -> Case:
+               ref_node: int = 2, steps: int = 1000, d_w: float = 0.5,
+               interp: str = "none") -> Case:
     """3-D D3Q19 full channel: walls at y = 0 and y = 2h, periodic in x and z.
 
-    Delta = 2h / ny; initial u_x = U_b (1 +/- 1 %) seeded; nu_tilde = 3 nu.
+    The boundary nodes lie d_w Delta from the walls (Section 4.1.2.5; d_w = 1/2
+    is the half-way placement), so 2h = (ny - 1 + 2 d_w) Delta; initial
+    u_x = U_b (1 +/- 1 %) seeded; nu_tilde = 3 nu.
     """
     h = 1.0
     p = channel_parameters(re_tau, h)
-    wall = BC(scheme, ref_node=ref_node)
+    wall = BC(scheme, ref_node=ref_node, d_w=d_w, interp=interp)
+    tag = "" if (d_w == 0.5 and interp == "none") else f"_{interp}_dw{d_w:g}"
     return Case(
-        name=f"channel_3d_Re{int(re_tau)}_{scheme}_{nx}x{ny}x{nz}", lattice="D3Q19",
-        nx=nx, ny=ny, nz=nz, dx=2.0 * h / ny, u_ref=p["u_b"], force=(p["g"], 0.0, 0.0),
+        name=f"channel_3d_Re{int(re_tau)}_{scheme}{tag}_{nx}x{ny}x{nz}", lattice="D3Q19",
+        nx=nx, ny=ny, nz=nz, dx=2.0 * h / (ny - 1 + 2.0 * d_w), u_ref=p["u_b"],
+        force=(p["g"], 0.0, 0.0),
         collision=collision, storage=storage, turbulence="sa", wall_law=wall_law,
         bcs={"ymin": wall, "ymax": dataclasses.replace(wall)},
         u_init=(p["u_b"], 0.0, 0.0), perturb=0.01, seed=seed, nut_ratio_init=3.0,

@@ -20,5 +20,5 @@ solver   -- the step in the paper's order: SA update, wall pre-pass, streaming,
 Parity status of each function is stated in its docstring; "parity unpinned"
 marks a function without an independent pin.
 """
-from . import lattice, wallfn, sa, solver  # noqa: F401
+from . import bounce, lattice, wallfn, sa, solver  # noqa: F401
 from .solver import Oracle  # noqa: F401

@@ -16,15 +16,19 @@ separate plain loop over the whole field, no fusion):
    tangential velocity u^n at the reference node (B or F) gives u_tau by Newton
    on the wall law; y_B+ = u_tau y_B / nu; nu_t|_B = nu kappa y_B+; the slip
    velocity is Eq. 35, u_w = u_B - u_tau^2 Delta_w / (nu + nu_t|_B) with
-   Delta_w = 1/2; rho_w = rho^n(B); the Dirichlet value nu_tilde_B = nu kappa y_B+.
+   Delta_w = d_w, the wall-to-B distance (1/2 for the half-way placement,
+   Section 4.1.2.5); rho_w = rho^n(B); the Dirichlet value
+   nu_tilde_B = nu kappa y_B+ with y_B = d_w.
 3. Streaming (Eq. 3) by pulling f*^n(x - c_i); periodic axes wrap; populations
    whose source lies outside a non-periodic face are unknown.
-4. y-face conditions: half-way bounce-back with the moving-wall term (Eq. 31),
+4. y-face conditions: half-way bounce-back with the moving-wall term (Eq. 31)
+   or its interpolated forms for d_w != 1/2 (Bouzidi, Eq. 36; Yu, Eq. 37),
    specular reflection (symmetry), or equilibrium at the free-stream state.
 5. x-face conditions: Zou-He velocity inlet, zero-gradient outlet (copy of the
    post-stream populations of the neighbouring column).
 6. Regularized (HRFD) wall nodes (Section 3.1): rho_F, u_F after streaming
-   (Eqs. 20-22); Newton at F; u_B = u_tau u+(y_B+) t; rho_B by Eq. 23; strain
+   (Eqs. 20-22); Newton at F (y_F = 1 + d_w); u_B = u_tau u+(y_B+) t with
+   y_B = d_w; rho_B by Eq. 23; strain
    rate with the blended wall-normal derivative of Eqs. 27-28 on the velocity
    of the previous step; all populations of B replaced by Eq. 19 with Eq. 26.
 7. Moments (Eqs. 4-5), nu_t^{n+1} = nu_tilde^{n+1} f_v1, omega from Eq. 8 with
@@ -38,6 +42,7 @@ import math
 
 import numpy as np
 
+from . import bounce as BB
 from . import lattice as L
 from . import sa as SA
 from .wallfn import KAPPA, WallLaw, solve_u_tau
@@ -77,6 +82,14 @@ class Oracle:
         for f in ("ymin", "ymax"):
             if bcs[f].kind in ("inlet_zouhe", "outlet_zerograd"):
                 raise ValueError("y faces: periodic, wall, symmetry or free stream")
+            b = bcs[f]
+            if b.kind in ("wall_bb", "wall_hrfd", "wall_cai_degrigny"):
+                if not (0.0 < b.d_w <= 1.0):
+                    raise ValueError("d_w must lie in (0, 1]")
+                if b.kind == "wall_bb" and b.interp == "none" and b.d_w != 0.5:
+                    raise ValueError("half-way bounce-back needs d_w = 1/2")
+            if b.interp != "none" and b.kind != "wall_bb":
+                raise ValueError("interpolation applies to bounce-back walls only")
         self.periodic = {ax: bcs[ax + "min"].kind == "periodic" for ax in "xyz"}
 
         # acoustic scaling (Section 4.1.1)
@@ -115,10 +128,11 @@ class Oracle:
         """1/d^2 with d the distance from the cell centre to the nearest wall
         (lattice units).  A wall face with a leading edge at x_start is the
         half-line x >= x_start; upstream cells measure to its edge point."""
-        y = np.arange(self.ny) + 0.5
+        j = np.arange(self.ny, dtype=np.float64)
         d = np.full((self.ny, self.nx), np.inf)
         for f in self.walls:
-            dy = y if f == "ymin" else self.ny - y
+            dw = self.bc[f].d_w
+            dy = j + dw if f == "ymin" else (self.ny - 1 - j) + dw
             xs = self.bc[f].x_start
             dxl = np.where(self.xc >= xs, 0.0, (self.xc - xs) / self.case.dx) if np.isfinite(xs) \
                 else np.zeros(self.nx)
@@ -190,16 +204,16 @@ class Oracle:
         row, s = self._row(face), self._inward(face)
         cols = self.walls[face]
         ref = row + s * (b.ref_node - 1)
-        y_ref = b.ref_node - 0.5
+        y_ref = (b.ref_node - 1) + b.d_w
         uB = self.u[:, :, row, :][:, :, cols]
         uR = self.u[:, :, ref, :][:, :, cols]
         ubt, _, _ = self._tangential(uB)
         _, U, t = self._tangential(uR)
         if self.turbulent:
             ut = solve_u_tau(self.law, U.ravel(), y_ref, self.nu).reshape(U.shape)
-            ypB = ut * 0.5 / self.nu
+            ypB = ut * b.d_w / self.nu
             nutB = self.nu * KAPPA * ypB
-            uw = ubt - (ut * ut * 0.5 / (self.nu + nutB))[None] * t
+            uw = ubt - (ut * ut * b.d_w / (self.nu + nutB))[None] * t
             tmp = nt_new[:, row, :]
             tmp[:, cols] = nutB
             nt_new[:, row, :] = tmp
@@ -211,6 +225,18 @@ class Oracle:
         full[:, cols] = ut
         self.utau[face] = full
         return uw, rho_w
+
+    def _link_neighbour(self, i, row):
+        """f*_i at x_F = x_B - c_i for every column of the boundary row, [z, x].
+        z wraps; x wraps when periodic, otherwise a link whose F node would leave
+        the lattice through an x face takes F in the boundary column itself
+        (zero gradient along x; reading)."""
+        cx, cy, cz = (int(v) for v in self.vs.c[i])
+        xs = np.arange(self.nx) - cx
+        xs = np.mod(xs, self.nx) if self.periodic["x"] else np.clip(xs, 0, self.nx - 1)
+        zs = np.mod(np.arange(self.nz) - cz, self.nz)
+        plane = self.fs[i][:, row - cy, :]
+        return plane[zs][:, xs]
 
     def stream(self):
         """Stage 3: f_i(x, t+1) = f*_i(x - c_i, t); unknowns are NaN."""
@@ -269,11 +295,19 @@ class Oracle:
             if b.kind == "wall_bb":
                 uw, rho_w = bb[face]
                 for i in toward:
+                    o = vs.opp[i]
                     cu = (vs.cf[i][:, None, None] * uw).sum(axis=0)
-                    val = self.fs[i][:, row, :][:, wallcols] - 2.0 * vs.w[i] * rho_w * cu / L.CS2
-                    cur = f[vs.opp[i]][:, row, :]
+                    mw = 2.0 * vs.w[i] * rho_w * cu / L.CS2
+                    fs_i_B = self.fs[i][:, row, :][:, wallcols]
+                    if b.interp == "none":
+                        val = BB.halfway(fs_i_B, mw)                       # Eq. 31
+                    else:
+                        fs_i_F = self._link_neighbour(i, row)[:, wallcols]
+                        fs_o_B = self.fs[o][:, row, :][:, wallcols]
+                        val = BB.RULES[b.interp](b.d_w, fs_i_B, fs_i_F, fs_o_B, mw)
+                    cur = f[o][:, row, :]
                     cur[:, wallcols] = val
-                    f[vs.opp[i]][:, row, :] = cur
+                    f[o][:, row, :] = cur
         return f
 
     def x_faces(self, f):
@@ -297,11 +331,12 @@ class Oracle:
                 f[j][:, :, -1] = f[j][:, :, -2]
         return f
 
-    def cai_degrigny_derivative(self, ut):
+    def cai_degrigny_derivative(self, ut, d_w=0.5):
         """Eq. 29: third-order one-sided difference of the wall function at B,
         (u_tau / Delta) (-11/6 u+(y_B+) + 3 u+(y_B+ + D+) - 3/2 u+(y_B+ + 2 D+)
-        + 1/3 u+(y_B+ + 3 D+)), Delta = 1 (lattice), D+ = u_tau / nu."""
-        yp = ut * 0.5 / self.nu
+        + 1/3 u+(y_B+ + 3 D+)), Delta = 1 (lattice), D+ = u_tau / nu,
+        y_B = d_w."""
+        yp = ut * d_w / self.nu
         dp = ut / self.nu
         up = self.law.u_plus
         return ut * (-11.0 / 6.0 * up(yp) + 3.0 * up(yp + dp) - 1.5 * up(yp + 2 * dp)
@@ -326,10 +361,10 @@ class Oracle:
             uF = (np.tensordot(vs.cf.T, fF, axes=(1, 0)) + 0.5 * self.F[:, None, None]) / rhoF
             _, U, t = self._tangential(uF)
             if self.turbulent:
-                ut = solve_u_tau(self.law, U.ravel(), 1.5, self.nu).reshape(U.shape)
+                ut = solve_u_tau(self.law, U.ravel(), 1.0 + b.d_w, self.nu).reshape(U.shape)
             else:
                 ut = np.zeros_like(U)
-            ypB = ut * 0.5 / self.nu
+            ypB = ut * b.d_w / self.nu
             uB = (ut * self.law.u_plus(ypB))[None] * t if self.turbulent else np.zeros_like(t)
             fB = f[:, :, row, :][:, :, cols]
             cn = vs.c[:, 1] * n_y
@@ -356,7 +391,7 @@ class Oracle:
                 uFFn = up[g][1:-1, yFF, 1:-1][:, cols]
                 fd = 0.5 * (-3.0 * uBn + 4.0 * uFn - uFFn)          # Eq. 28
                 if g != 1 and self.turbulent and cai:
-                    dn = self.cai_degrigny_derivative(ut) * t[g]          # Eqs. 29-30
+                    dn = self.cai_degrigny_derivative(ut, b.d_w) * t[g]   # Eqs. 29-30
                 elif g != 1 and self.turbulent:
                     ana = np.where(ut > 0, ut * ut / self.nu * dup, 0.0) * t[g]   # Eq. 15
                     dn = b.beta * ana + (1.0 - b.beta) * fd               # Eq. 27
