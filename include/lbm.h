@@ -66,6 +66,15 @@ enum {
                                   the wall function, Eqs. 29-30 */
 };
 
+/* bounce-back wall whose boundary nodes are not half-way from the wall
+   (lbm_bc.interp; Section 3.2): the reflected population of each crossing link
+   is interpolated along the link at the wall fraction q = d_w */
+enum {
+  LBM_IBB_NONE = 0,            /* half-way bounce-back, Eq. 31 (d_w must be 1/2) */
+  LBM_IBB_BOUZIDI = 1,         /* Bouzidi et al., Eq. 36 (two branches at q = 1/2) */
+  LBM_IBB_YU = 2               /* Yu et al., Eq. 37 (one expression for every q) */
+};
+
 /* faces (lbm_set_bc face argument) */
 enum { LBM_XMIN = 0, LBM_XMAX = 1, LBM_YMIN = 2, LBM_YMAX = 3, LBM_ZMIN = 4, LBM_ZMAX = 5 };
 
@@ -116,6 +125,14 @@ typedef struct {
                                   cells before it behave as a symmetry plane */
   double u_in[3];              /* inlet / free-stream velocity, m/s */
   double nut_ratio_in;         /* inlet / free-stream nu_tilde / nu */
+  double d_w;                  /* walls: distance from the wall to the boundary nodes in
+                                  lattice spacings, (0, 1]; 0 selects the half-way 1/2.
+                                  It sets y_B = d_w Delta in the wall function, Delta_w
+                                  in Eq. 35, Newton's reference height, the SA wall
+                                  distance and the bounce-back link fraction q
+                                  (Section 4.1.2.5) */
+  int interp;                  /* bounce-back walls: LBM_IBB_*; d_w != 1/2 needs
+                                  LBM_IBB_BOUZIDI or LBM_IBB_YU */
 } lbm_bc;
 
 typedef struct {

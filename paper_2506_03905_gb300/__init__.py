@@ -43,6 +43,7 @@ TURBULENCE = {"sa": 0, "laminar": 1}
 WALL_LAW = {"sa_analytic": 0, "log": 1}
 BC_KIND = {"periodic": 0, "wall_bb": 1, "wall_hrfd": 2, "symmetry": 3, "inlet_zouhe": 4,
            "outlet_zerograd": 5, "freestream": 6, "wall_cai_degrigny": 7}
+IBB = {"none": 0, "bouzidi": 1, "yu": 2}
 FACES = ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")
 FIELD = {"rho": 1 << 0, "u": 1 << 1, "nu_t": 1 << 2, "nu_tilde": 1 << 3,
          "u_tau_ymin": 1 << 4, "u_tau_ymax": 1 << 5, "cf_ymin": 1 << 6, "cf_ymax": 1 << 7}
@@ -68,7 +69,7 @@ class LbmBC(ctypes.Structure):
     _fields_ = [
         ("kind", ctypes.c_int), ("beta", ctypes.c_double), ("ref_node", ctypes.c_int),
         ("x_start", ctypes.c_double), ("u_in", ctypes.c_double * 3),
-        ("nut_ratio_in", ctypes.c_double),
+        ("nut_ratio_in", ctypes.c_double), ("d_w", ctypes.c_double), ("interp", ctypes.c_int),
     ]
 
 
@@ -278,6 +279,8 @@ def bc_struct(bc) -> LbmBC:
     b.x_start = bc.x_start if math.isfinite(bc.x_start) else -math.inf
     b.u_in = (ctypes.c_double * 3)(*bc.u_in)
     b.nut_ratio_in = bc.nut_ratio_in
+    b.d_w = bc.d_w
+    b.interp = IBB[bc.interp]
     return b
 
 

@@ -193,6 +193,7 @@ extern "C" lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     c->bc[f].ref_node = 2;
     c->bc[f].x_start = -INFINITY;
     c->bc[f].nut_ratio_in = 3.0;
+    c->bc[f].d_w = 0.5;
   }
   c->stream = (cudaStream_t)k.stream;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -275,13 +276,60 @@ extern "C" lbm_status lbm_set_bc(lbm_ctx* c, int face, const lbm_bc* bc) {
     lbm_ctx_set_error(c, "beta must lie in [0, 1]");
     return LBM_EINVAL;
   }
+  const double d_w = bc->d_w == 0.0 ? 0.5 : bc->d_w;
+  if (wall && !(d_w > 0.0 && d_w <= 1.0)) {
+    lbm_ctx_set_error(c, "d_w must lie in (0, 1]");
+    return LBM_EINVAL;
+  }
+  if (bc->interp < LBM_IBB_NONE || bc->interp > LBM_IBB_YU ||
+      (bc->interp != LBM_IBB_NONE && kd != LBM_BC_WALL_SLIP_BB)) {
+    lbm_ctx_set_error(c, "interp is LBM_IBB_NONE, _BOUZIDI or _YU, on bounce-back walls only");
+    return LBM_EINVAL;
+  }
+  if (kd == LBM_BC_WALL_SLIP_BB && bc->interp == LBM_IBB_NONE && d_w != 0.5) {
+    lbm_ctx_set_error(c, "half-way bounce-back needs d_w = 1/2 (use an interpolated rule)");
+    return LBM_EINVAL;
+  }
   c->bc[face] = *bc;
+  c->bc[face].d_w = d_w;
   c->finalized = false;
   c->gvalid[0] = c->gvalid[1] = false;
   return LBM_OK;
 }
 
 static void build_tensor_maps(lbm_ctx* c);
+
+// Weights (a_o, a_F, a_i, a_K) of a face's bounce-back rule in deviation form,
+// h_i(B, t+1) = a_o h*_opp(B) + a_F h*_opp(B + c_i) + a_i h*_i(B) + a_K K, for
+// the incoming direction i, K = 6 w_i (rho_w c_i.u_w - c_ix U) (the moving-wall
+// term plus the change of reference equilibrium from opp(i) to i).  Every rule
+// is affine with weights summing to one, so the reference equilibria enter only
+// through K.  q is the link fraction d_w.
+//   Eq. 31 (half-way): h*_opp(B) + K.
+//   Eq. 36, q >= 1/2: (h*_opp(B) + K) / 2q + (1 - 1/2q) h*_i(B)   [h*_i(B) = h_i(F, t+1)]
+//   Eq. 36, q <  1/2: 2q h*_opp(B) + (1 - 2q) h*_opp(F) + K       [F = B + c_i]
+//   Eq. 37: the wall-point value W = q h*_opp(B) + (1 - q) h*_opp(F) + K (the
+//     streamed population interpolated to the wall and bounced back), then
+//     W + r (h*_i(B) - W) with r = q / (1 + q).
+static void ibb_weights(int interp, double q, double a[4]) {
+  a[0] = 1.0;
+  a[1] = 0.0;
+  a[2] = 0.0;
+  a[3] = 1.0;
+  if (interp == LBM_IBB_BOUZIDI && q >= 0.5) {
+    a[0] = a[3] = 1.0 / (2.0 * q);
+    a[2] = 1.0 - 1.0 / (2.0 * q);
+  } else if (interp == LBM_IBB_BOUZIDI) {
+    a[0] = 2.0 * q;
+    a[1] = 1.0 - 2.0 * q;
+  } else if (interp == LBM_IBB_YU) {
+    const double r = q / (1.0 + q);
+    a[0] = q * (1.0 - r);
+    a[1] = (1.0 - q) * (1.0 - r);
+    a[2] = r;
+    a[3] = 1.0 - r;
+  }
+}
 
 // Validate the face combination and build the kernel parameters.
 lbm_status lbm_ctx_finalize(lbm_ctx* c) {
@@ -334,6 +382,9 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
     p.xs_lb[fi] = std::isfinite(b.x_start) ? (b.x_start - k.origin[0]) / k.dx : -1e30;
     p.beta[fi] = b.beta;
     p.ref_node[fi] = b.ref_node;
+    p.d_w[fi] = b.d_w;
+    p.interp[fi] = b.kind == LBM_BC_WALL_SLIP_BB ? b.interp : LBM_IBB_NONE;
+    ibb_weights(p.interp[fi], b.d_w, p.ibb[fi]);
     p.nwall[fi] = (c->nx - x0) * c->nz;
     if (p.nwall[fi] > 0) p.wall[fi] = b.kind;
     if (b.kind == LBM_BC_WALL_HRFD || b.kind == LBM_BC_WALL_CAI_DEGRIGNY) ++nhrfd;
@@ -373,7 +424,11 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
   p.Ush_f = (float)p.Ush;
   for (int a = 0; a < 3; ++a) p.F_f[a] = (float)p.F[a];
   for (int i = 0; i < 19; ++i) p.guoA_f[i] = (float)p.guoA[i];
-  for (int f = 0; f < 2; ++f) p.xs_lb_f[f] = (float)p.xs_lb[f];
+  for (int f = 0; f < 2; ++f) {
+    p.xs_lb_f[f] = (float)p.xs_lb[f];
+    p.d_w_f[f] = (float)(p.wall[f] ? p.d_w[f] : 0.5);
+    for (int k = 0; k < 4; ++k) p.ibb_f[f][k] = (float)p.ibb[f][k];
+  }
   for (int j = 0; j < 4; ++j) {
     p.nt_face_f[j] = (float)p.nt_face[j];
     for (int a = 0; a < 3; ++a) p.u_face_f[j][a] = (float)p.u_face[j][a];

@@ -130,7 +130,8 @@ struct Params {
   double Ush;                  // reference velocity U (x) of the stored deviations
   // float copies for the FP32 kernels: converting a double per thread would run
   // on the FP64 pipe, which on GB300 has 1/64 of the FP32 rate
-  float nu_f, F_f[3], guoA_f[19], Ush_f, xs_lb_f[2], u_face_f[4][3], nt_face_f[4];
+  float nu_f, F_f[3], guoA_f[19], Ush_f, xs_lb_f[2], u_face_f[4][3], nt_face_f[4], d_w_f[2],
+      ibb_f[2][4];
   double law_kappa, law_B;
   int kind[6];                 // face kinds
   int px, py;                  // x / y periodic
@@ -140,6 +141,13 @@ struct Params {
   double xs_lb[2];             // leading edge position in lattice units from the x face
   double beta[2];
   int ref_node[2];
+  double d_w[2];               // wall-to-boundary-node distance / Delta (1/2: half-way)
+  int interp[2];               // bounce-back walls: 0 half-way, 1 Bouzidi, 2 Yu
+  // bounce-back rule of each y face as affine weights (a_o, a_F, a_i, a_K) of
+  //   h_i(B) = a_o h*_opp(B) + a_F h*_opp(B + c_i) + a_i h*_i(B) + a_K K,
+  //   K = 6 w_i (rho_w c_i.u_w - c_ix U)
+  // for an incoming direction i (Eq. 31: 1, 0, 0, 1; Eqs. 36-37: ibb_weights)
+  double ibb[2][4];
   int nwall[2];                // (nx - xw0) * nz wall nodes
   double u_face[4][3];         // prescribed velocity of xmin, xmax, ymin, ymax
   double nt_face[4];           // prescribed nu_tilde of xmin, xmax, ymin, ymax
@@ -284,7 +292,8 @@ template <class R> __device__ __forceinline__ R inv_wall_dist2(const Params& p, 
 #pragma unroll
   for (int f = 0; f < 2; ++f) {
     if (p.wall[f]) {
-      const R dy = f == 0 ? (R)y + (R)0.5 : (R)(p.ny - y) - (R)0.5;
+      const R dw = psel<R>(p.d_w[f], p.d_w_f[f]);
+      const R dy = f == 0 ? (R)y + dw : (R)(p.ny - 1 - y) + dw;
       R e = dy * dy;
       if (x < p.xw0[f]) {
         const R dxl = ((R)x + (R)0.5) - psel<R>(p.xs_lb[f], p.xs_lb_f[f]);
@@ -541,8 +550,22 @@ __device__ typename Compute<ST>::R pull_bc(const Params& p, int x, int y, int z,
     const R* uw = (const R*)p.uw[fi] + 3 * node;
     const R cu = (R)cx * uw[0] + (R)cy * uw[1] + (R)cz * uw[2];
     const R rw = ((const R*)p.rhow[fi])[node];
-    return (R)C::ld(f + opp(i) * p.ncell + cidx(p, x, y, z)) +
-           (R)6 * (R)L::w(i) * (rw * cu - (R)cx * psel<R>(p.Ush, p.Ush_f));
+    const long long idB = cidx(p, x, y, z);
+    const R K = (R)6 * (R)L::w(i) * (rw * cu - (R)cx * psel<R>(p.Ush, p.Ush_f));
+    const R hoB = (R)C::ld(f + opp(i) * p.ncell + idB);
+    if (p.interp[fi] == 0) return hoB + K;
+    // Eqs. 36-37: the F node of the link is B + c_i (one link into the fluid);
+    // z wraps, x wraps when periodic and otherwise stays in the boundary column
+    int xf = x + cx;
+    if (xf < 0 || xf >= p.nx) xf = p.px ? (xf < 0 ? xf + p.nx : xf - p.nx) : x;
+    int zf = z + cz;
+    zf = zf < 0 ? zf + p.nz : (zf >= p.nz ? zf - p.nz : zf);
+    const R hoF = (R)C::ld(f + opp(i) * p.ncell + cidx(p, xf, y + cy, zf));
+    const R hiB = (R)C::ld(f + i * p.ncell + idB);
+    const double* a = p.ibb[fi];
+    const float* af = p.ibb_f[fi];
+    return psel<R>(a[0], af[0]) * hoB + psel<R>(a[1], af[1]) * hoF + psel<R>(a[2], af[2]) * hiB +
+           psel<R>(a[3], af[3]) * K;
   }
   if (wall_col) {  // regularized walls: every population of B is rebuilt later
     *known = false;

@@ -174,8 +174,10 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
     return;
   }
   if (p.px && p.turbulent && p.ny >= 3) {
-    const int fw = (y == 0 && p.wall[0] == BC_WALL_BB && x >= p.xw0[0]) ? 0
-                 : ((y == p.ny - 1 && p.wall[1] == BC_WALL_BB && x >= p.xw0[1]) ? 1 : -1);
+    // half-way slip bounce-back rows (the interpolated rules take the general path)
+    const int fw = (y == 0 && p.wall[0] == BC_WALL_BB && p.interp[0] == 0 && x >= p.xw0[0]) ? 0
+                 : ((y == p.ny - 1 && p.wall[1] == BC_WALL_BB && p.interp[1] == 0 &&
+                     x >= p.xw0[1]) ? 1 : -1);
     if (fw >= 0) {
       bulk_wall_bb<Q, ST>(p, fw, x, y, z);
       return;
@@ -450,7 +452,8 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
   if (p.wall[fi] == BC_WALL_BB) {
     // Section 3.2: u_tau from the tangential velocity at the reference node
     const int yR = yB + s * (p.ref_node[fi] - 1);
-    const double yref = (double)p.ref_node[fi] - 0.5;
+    const double dw = p.d_w[fi];                       // y_B (1/2 half-way)
+    const double yref = (double)(p.ref_node[fi] - 1) + dw;
     const long long idR = cidx(p, x, yR, z);
     const double Ux = (double)us[idR], Uz = (double)us[idR + 2 * p.ncell];
     const double U = sqrt(Ux * Ux + Uz * Uz);
@@ -458,10 +461,10 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     R* uw = (R*)p.uw[fi] + 3 * node;
     if (p.turbulent) {
       ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, U, yref, nu, p.utau[fi][node], &ut);
-      const double ypB = ut * 0.5 / nu;
+      const double ypB = ut * dw / nu;
       const double nutB = nu * WF::kappa * ypB;
-      // Eq. 35 with Delta_w = 1/2 and nu_t|_B = nu kappa y_B+
-      const double slip = ut * ut * 0.5 / (nu + nutB);
+      // Eq. 35 with Delta_w = y_B = d_w and nu_t|_B = nu kappa y_B+
+      const double slip = ut * ut * dw / (nu + nutB);
       uw[0] = (R)((double)us[idB] - slip * tx);
       uw[1] = (R)0;
       uw[2] = (R)((double)us[idB + 2 * p.ncell] - slip * tz);
@@ -490,9 +493,10 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const double Ux = ((double)jF[0] + p.Ush) / (double)rhoF, Uz = (double)(jF[2] / rhoF);
     const double U = sqrt(Ux * Ux + Uz * Uz);
     const double tx = U > 0.0 ? Ux / U : 1.0, tz = U > 0.0 ? Uz / U : 0.0;
+    const double dw = p.d_w[fi];                       // y_B; y_F = 1 + d_w
     if (p.turbulent)
-      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, U, 1.5, nu, p.utau[fi][node], &ut);
-    const double ypB = ut * 0.5 / nu;
+      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, U, 1.0 + dw, nu, p.utau[fi][node], &ut);
+    const double ypB = ut * dw / nu;
     const double upB = p.turbulent ? ut * wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB) : 0.0;
     const R uB[3] = {(R)(upB * tx), (R)0, (R)(upB * tz)};
     // Eq. 23 with u_B . n = 0: rho_B = f_par + 2 f_perp (deviations: weights sum to 1)
