@@ -660,40 +660,65 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
     }
     return;
   }
-  // regularized: non-equilibrium moments first, then the rebuilt populations
-  R geq[Q];
+  // regularized, over opposite pairs as above.  With n = h - h^eq, a pair enters
+  // the non-equilibrium moments only through s = n_i + n_opp (second order,
+  // sum c_a c_b n) and d = n_i - n_opp (first order, sum c n); the rest
+  // population enters neither.  The rebuilt populations are
+  //   h*_{i / opp} = h^eq + (delta - 1) P + forcing,  P = w (3 c.a + 4.5 Q:Pi),
+  // whose even part is 4.5 w Q_i:Pi and odd part 3 w c_i.a.
+  const R dm1 = delta - (R)1;
+  R ax = 0, ay = 0, az = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i)
-    geq[i] = heq_cdu<Q, R>(i, cdot<Q, R>(i, dux, uy, uz), drho, U, one_m_uu15, du15);
-  R a[3] = {0, 0, 0}, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const R n = g[i] - geq[i];
+  for (int i = 1; i < Q; i += 2) {
+    const R w = (R)L::w(i);
+    const R cdu = cdot<Q, R>(i, dux, uy, uz);
+    const R cU = L::c(i, 0) > 0 ? U : (L::c(i, 0) < 0 ? -U : (R)0);
+    const R su = cU + cdu;
+    const R ev = w * (drho * ((R)4.5 * su * su + one_m_uu15) + ((R)4.5 * cdu * (su + cU) - du15));
+    const R od = w * (R)3 * (drho * su + cdu);
+    const R sp = (g[i] + g[i + 1]) - (R)2 * ev;
+    const R dp = (g[i] - g[i + 1]) - (R)2 * od;
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-    a[0] += (R)cx * n;
-    a[1] += (R)cy * n;
-    a[2] += (R)cz * n;
-    pxx += (R)(cx * cx) * n;
-    pyy += (R)(cy * cy) * n;
-    pzz += (R)(cz * cz) * n;
-    pxy += (R)(cx * cy) * n;
-    pxz += (R)(cx * cz) * n;
-    pyz += (R)(cy * cz) * n;
+    if (cx) ax += cx > 0 ? dp : -dp;
+    if (cy) ay += cy > 0 ? dp : -dp;
+    if (cz) az += cz > 0 ? dp : -dp;
+    if (cx) pxx += sp;
+    if (cy) pyy += sp;
+    if (cz) pzz += sp;
+    if (cx && cy) pxy += cx * cy > 0 ? sp : -sp;
+    if (cx && cz) pxz += cx * cz > 0 ? sp : -sp;
+    if (cy && cz) pyz += cy * cz > 0 ? sp : -sp;
+    g[i] = ev;       // the equilibrium parts are all the rebuild needs
+    g[i + 1] = od;
   }
   const R tr = (pxx + pyy + pzz) * ((R)1 / (R)3);
+  {
+    const R wgt0 = (R)L::w(0);
+    R gi = wgt0 * (drho * one_m_uu15 - du15) + dm1 * (wgt0 * (R)4.5 * -tr);
+    if (p.has_force) gi -= fpre * wgt0 * uF3;
+    g[0] = gi;
+  }
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  for (int i = 1; i < Q; i += 2) {
+    const R w = (R)L::w(i);
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-    const R qp = (R)(cx * cx) * pxx + (R)(cy * cy) * pyy + (R)(cz * cz) * pzz +
-                 (R)2 * ((R)(cx * cy) * pxy + (R)(cx * cz) * pxz + (R)(cy * cz) * pyz) - tr;
-    const R ca = (R)cx * a[0] + (R)cy * a[1] + (R)cz * a[2];
-    const R P = (R)L::w(i) * ((R)3 * ca + (R)4.5 * qp);
-    R gi = (geq[i] - P) + delta * P;
+    R qp = -tr, ca = 0;
+    if (cx) { qp += pxx; ca += cx > 0 ? ax : -ax; }
+    if (cy) { qp += pyy; ca += cy > 0 ? ay : -ay; }
+    if (cz) { qp += pzz; ca += cz > 0 ? az : -az; }
+    if (cx && cy) qp += (R)2 * (cx * cy > 0 ? pxy : -pxy);
+    if (cx && cz) qp += (R)2 * (cx * cz > 0 ? pxz : -pxz);
+    if (cy && cz) qp += (R)2 * (cy * cz > 0 ? pyz : -pyz);
+    R E = g[i] + dm1 * (w * (R)4.5 * qp);
+    R O = g[i + 1] + dm1 * (w * (R)3 * ca);
     if (p.has_force) {
-      const R cu = (cx > 0 ? U : (cx < 0 ? -U : (R)0)) + cdot<Q, R>(i, dux, uy, uz);
-      gi += fpre * (psel<R>(p.guoA[i], p.guoA_f[i]) * ((R)1 + (R)3 * cu) - (R)L::w(i) * uF3);
+      const R A = psel<R>(p.guoA[i], p.guoA_f[i]);
+      const R su = (cx > 0 ? U : (cx < 0 ? -U : (R)0)) + cdot<Q, R>(i, dux, uy, uz);
+      E += fpre * ((R)3 * su * A - w * uF3);
+      O += fpre * A;
     }
-    g[i] = gi;
+    g[i] = E + O;
+    g[i + 1] = E - O;
   }
 }
 
