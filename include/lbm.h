@@ -184,6 +184,24 @@ lbm_status lbm_fields(lbm_ctx* ctx, unsigned mask, void* const* dst, int dst_on_
    memory.  Synchronises cfg.stream. */
 lbm_status lbm_diagnostics(lbm_ctx* ctx, lbm_diag* out);
 
+/* Convergence-driven run (Section 4.1.1: runs are converged when the relative
+   change of u_tau falls below 1e-4).  Advances in chunks of check_every steps
+   (the last chunk may be shorter); after each chunk the largest relative change
+   of u_tau over the wall nodes since the previous check,
+   max |u_tau - u_tau_prev| / u_tau, is compared with tol, and the run stops at
+   the first check below tol or after max_steps steps.  The paper states the
+   criterion per iteration; a chunk of m steps applies it to the change over m
+   steps (m = 1 is the literal per-step form).  The u_tau of the state at entry
+   is the first reference, so a run stops after one chunk at the earliest.
+   *steps_done receives the steps taken and *residual the last checked change
+   (converged if and only if *residual < tol; INFINITY before the first check).
+   Synchronises cfg.stream once per chunk.  Errors: LBM_EINVAL for tol <= 0,
+   check_every < 1, max_steps < 0, NULL outputs, no state yet, or a lattice
+   without walls; LBM_ENONFINITE when a wall u_tau is NaN/Inf; step errors as
+   lbm_step.  Resets the reference of lbm_diagnostics' max_rel_du_tau. */
+lbm_status lbm_run_to_convergence(lbm_ctx* ctx, double tol, int check_every, long long max_steps,
+                                  long long* steps_done, double* residual);
+
 /* Raw state for checkpointing: the post-collision populations in storage
    precision (bytes reported by lbm_state_bytes), the stored velocity and
    nu_tilde in compute precision and u_tau in FP64, concatenated.  dst and src

@@ -26,7 +26,7 @@ __all__ = [
     "lbm_diagnostics", "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_destroy",
     "lbm_last_error", "lbm_lattice_params", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tune", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_moments_noalloc",
-    "lbm_kernel_launches",
+    "lbm_kernel_launches", "lbm_run_to_convergence",
 ]
 
 LIB_PATH = _build.LIB
@@ -116,6 +116,9 @@ def lib():
         "lbm_destroy": (None, [_P]),
         "lbm_last_error": (ctypes.c_char_p, [_P]),
         "lbm_kernel_launches": (ctypes.c_ulonglong, [_P]),
+        "lbm_run_to_convergence": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int,
+                                                  ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
+                                                  ctypes.POINTER(ctypes.c_double)]),
         "lbm_lattice_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
         "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
         "lbm_batch_step": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -200,6 +203,16 @@ def lbm_destroy(ctx):
 def lbm_last_error(ctx=None) -> str:
     s = lib().lbm_last_error(ctx)
     return s.decode() if s else ""
+
+
+def lbm_run_to_convergence(ctx, tol: float = 1e-4, check_every: int = 1000,
+                           max_steps: int = 1_000_000):
+    """Returns (steps taken, last relative u_tau change); see include/lbm.h."""
+    n = ctypes.c_longlong(0)
+    r = ctypes.c_double(0.0)
+    _check(lib().lbm_run_to_convergence(ctx, tol, check_every, max_steps, ctypes.byref(n),
+                                        ctypes.byref(r)), "lbm_run_to_convergence", ctx)
+    return int(n.value), float(r.value)
 
 
 def lbm_kernel_launches(ctx) -> int:
@@ -380,6 +393,10 @@ class Solver:
 
     def lattice_params(self):
         return lbm_lattice_params(self.ctx)
+
+    def run_to_convergence(self, tol: float = 1e-4, check_every: int = 1000,
+                           max_steps: int = 1_000_000):
+        return lbm_run_to_convergence(self.ctx, tol, check_every, max_steps)
 
     def kernel_launches(self) -> int:
         return lbm_kernel_launches(self.ctx)

@@ -847,6 +847,47 @@ extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out) {
   return s == LBM_ENONFINITE ? LBM_OK : s;
 }
 
+extern "C" lbm_status lbm_run_to_convergence(lbm_ctx* c, double tol, int check_every,
+                                             long long max_steps, long long* steps_done,
+                                             double* residual) {
+  if (!c || !(tol > 0.0) || check_every < 1 || max_steps < 0 || !steps_done || !residual)
+    return LBM_EINVAL;
+  if (!c->ready) {
+    lbm_ctx_set_error(c, "lbm_set_fields (or lbm_set_state) must come first");
+    return LBM_EINVAL;
+  }
+  lbm_status s = lbm_ctx_finalize(c);
+  if (s != LBM_OK) return s;
+  if (!(c->base.wall[0] || c->base.wall[1])) {
+    lbm_ctx_set_error(c, "the convergence test needs a wall (it watches u_tau)");
+    return LBM_EINVAL;
+  }
+  *steps_done = 0;
+  *residual = INFINITY;
+  // the u_tau of the starting state is the first reference
+  launch_wall_stats(lbm_ctx_params(c, c->cur), c->utau_prev, c->red_out + 8, c->stream);
+  ++c->launches;
+  long long done = 0;
+  double res = INFINITY;
+  while (done < max_steps) {
+    const int n = (int)std::min<long long>(check_every, max_steps - done);
+    s = lbm_step(c, n);
+    if (s != LBM_OK) return s;
+    done += n;
+    launch_wall_stats(lbm_ctx_params(c, c->cur), c->utau_prev, c->red_out + 8, c->stream);
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(&res, c->red_out + 10, sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+    s = check_flags(c);   // synchronises the stream
+    *steps_done = done;
+    *residual = res;
+    if (s != LBM_OK) return s;
+    if (res < tol) break;
+  }
+  return LBM_OK;
+}
+
 extern "C" size_t lbm_state_bytes(const lbm_ctx* c) {
   if (!c) return 0;
   return (size_t)c->Q * c->ncell * c->esz + (size_t)4 * c->ncell * c->rsz +

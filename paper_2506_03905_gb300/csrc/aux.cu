@@ -25,6 +25,7 @@ __global__ void k_wall_stats(const Params p, double* prev, double* out) {
       const double pv = prev[f * (long long)p.nx * p.nz + k];
       acc[0] += ut;
       if (ut > 0.0) acc[1] = fmax(acc[1], fabs(ut - pv) / ut);
+      if (!isfinite(ut)) atomicOr(p.flags, FLAG_NONFINITE);
       prev[f * (long long)p.nx * p.nz + k] = ut;
     }
     sh[0][threadIdx.x] = acc[0];
