@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 if "reference" in sys.argv:
-    # the CPU reference arm reports one core: keep numpy's thread pools at one
+    # each oracle copy of the CPU reference arm runs on one core: one numpy thread
     for _k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[_k] = "1"
 
@@ -40,7 +40,11 @@ import numpy as np  # noqa: E402
 import lbm_cases as C  # noqa: E402
 
 METRIC = "MLUPS and % of HBM roofline: FP32 vs FP16-storage vs batched, at C_f err ≤1%"
-WORKLOAD = dict(re_tau=5200.0, scheme="wall_bb", nx=256, ny=128, nz=128, seed=0)
+# slip-velocity bounce-back with Yu's rule at the half-way position: plain
+# half-way bounce-back (Eq. 31) develops a growing wall-row oscillation on this
+# 3-D channel (in FP64 as in FP32), which Yu's rule damps
+WORKLOAD = dict(re_tau=5200.0, scheme="wall_bb", nx=256, ny=128, nz=128, seed=0, d_w=0.5,
+                interp="yu")
 # algorithmic bytes per cell per step: read + write every population once,
 # read + write nu_tilde once (velocity and nu_t are recomputable, the wall
 # distance is analytic)
@@ -99,7 +103,7 @@ class ClockSampler:
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -255,6 +259,8 @@ def run_ours(args):
                           ("fp16_hrfd", dict(scheme="wall_hrfd", storage="fp16"))]:
             wk = dict(WORKLOAD)
             wk.update({k: v for k, v in kw.items() if k != "storage"})
+            if wk["scheme"] != "wall_bb":
+                wk["interp"] = "none"        # interpolation applies to bounce-back walls
             vc = C.channel_3d(**wk, storage=kw["storage"])
             vms, vbulk, vwall, vd = time_case(pkg, vc, vsteps, 3, torch)
             vb = ALG_BYTES[(vc.lattice, vc.storage)] * vc.cells
@@ -275,19 +281,23 @@ def run_ours(args):
                 "alg_bytes_per_cell": ALG_BYTES[(pc.lattice, pc.storage)],
                 "bulk_frac_of_hbm": round(pb / (pbulk * 1e-3) / 1e9 / peak, 4),
                 "nonfinite": int(pd.nonfinite)}
-        try:
-            variants.update(batched_variant(pkg, torch, vsteps))
-        except Exception as exc:  # the batched path reports its own status
-            variants["batched"] = {"unavailable": str(exc)[:200]}
+        for storage in ("fp32", "fp16"):
+            try:
+                variants.update(batched_variant(pkg, torch, vsteps, storage=storage))
+            except Exception as exc:  # the batched path reports its own status
+                variants[f"batched_{storage}"] = {"unavailable": str(exc)[:200]}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "channel_3d_D3Q19_256x128x128_fp32_Re5200_slip_bounce_back",
+        "config": {"workload": "channel_3d_D3Q19_256x128x128_fp32_Re5200_slip_bounce_back_yu",
                    "lattice": "D3Q19", "nx": 256, "ny": 128, "nz": 128, "storage": "fp32",
-                   "collision": "bgk", "walls": "slip-velocity bounce-back (Eq. 35) both y faces",
+                   "collision": "bgk",
+                   "walls": "slip-velocity bounce-back (Eq. 35) with Yu's rule (Eq. 37) at "
+                            "d_w = 1/2, both y faces",
+                   "init": "u_x = U_b (1 +/- 1 %) seeded, nu_tilde = max(3 nu, kappa u_tau d)",
                    "turbulence": "Spalart-Allmaras", "cells": cells,
                    "l2": "inputs larger than L2 (2 x 319 MB population buffers)",
                    "parallelism": f"replicas x{world}"},
@@ -299,6 +309,7 @@ def run_ours(args):
         "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "status": int(st)},
         "gpu_launches": int(n_launches),
+        **({"error": "non-finite state after the timed steps"} if diag.nonfinite else {}),
         "clocks": clk,
         "diagnostics": {"mass": diag.mass, "nonfinite": int(diag.nonfinite),
                         "mean_u_tau": list(diag.mean_u_tau)},
@@ -313,8 +324,8 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def batched_variant(pkg, torch, steps, rank=0, world=1):
-    cases = C.batched_sweep(96, storage="fp32")
+def batched_variant(pkg, torch, steps, rank=0, world=1, storage="fp32"):
+    cases = C.batched_sweep(96, storage=storage)
     if world > 1:   # instances are independent: each rank advances its own shard
         mine = C.shard_instances([c.cells for c in cases], world, rank)
         cases = [cases[i] for i in mine]
@@ -334,8 +345,8 @@ def batched_variant(pkg, torch, steps, rank=0, world=1):
         s.step(steps)
     torch.cuda.synchronize()
     seq = time.perf_counter() - t0
-    out["per_case_fp32"] = {"mlups": round(total * steps / seq / 1e6, 1), "instances": len(cases),
-                            "cells": total}
+    out[f"per_case_{storage}"] = {"mlups": round(total * steps / seq / 1e6, 1),
+                                  "instances": len(cases), "cells": total}
     b = pkg.lbm_batch_create([s.ctx for s in solvers])
     try:
         pkg.lbm_batch_step(b, 2)
@@ -344,8 +355,8 @@ def batched_variant(pkg, torch, steps, rank=0, world=1):
         pkg.lbm_batch_step(b, steps)
         torch.cuda.synchronize()
         bt = time.perf_counter() - t0
-        out["batched_fp32"] = {"mlups": round(total * steps / bt / 1e6, 1), "instances": len(cases),
-                               "cells": total}
+        out[f"batched_{storage}"] = {"mlups": round(total * steps / bt / 1e6, 1),
+                                     "instances": len(cases), "cells": total}
     finally:
         pkg.lbm_batch_destroy(b)
         for s in solvers:
@@ -378,49 +389,97 @@ print(json.dumps(dict(steps=n, seconds=dt, cells=case.cells)))
 """
 
 
-def cpu_baseline(seconds: float):
+def host_cores() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def _oracle_workers(code: str, n: int):
+    """Run n single-threaded copies of an oracle snippet at once (one per host
+    core, fresh interpreters) and return their JSON results."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env) for _ in range(n)]
+    out = []
+    for pr in procs:
+        so, se = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(se[-300:])
+        out.append(json.loads(so.strip().splitlines()[-1]))
+    return out
+
+
+def cpu_baseline(seconds: float):
+    """The oracle on the host cores: one copy per core on its own crop, all at
+    once (weak scaling; cells x steps summed, divided by the longest run), then
+    one copy alone for the single-core figure."""
     code = _CPU_SNIPPET.format(root=ROOT, seconds=seconds)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        return {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                "error": r.stderr[-300:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": round(d["cells"] * d["steps"] / d["seconds"] / 1e6, 4), "unit": "MLUPS",
-            "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, same channel physics on a 64x128x8 crop, "
-                      f"{d['steps']} steps in {d['seconds']:.1f} s (one thread)"}
+    n = host_cores()
+    try:
+        allc = _oracle_workers(code, n)
+        one = _oracle_workers(code, 1)[0]
+    except Exception as exc:
+        return {"value": None, "unit": "MLUPS", "cores": n, "kind": "oracle", "error": str(exc)}
+    value = sum(d["cells"] * d["steps"] for d in allc) / max(d["seconds"] for d in allc) / 1e6
+    single = one["cells"] * one["steps"] / one["seconds"] / 1e6
+    return {"value": round(value, 4), "unit": "MLUPS", "cores": n, "kind": "oracle",
+            "single_core": round(single, 4),
+            "sample": f"FP64 numpy oracle, same channel physics on a 64x128x8 crop per core, "
+                      f"{n} single-threaded copies for ~{seconds:.0f} s "
+                      f"({sum(d['steps'] for d in allc)} crop steps); single core alone "
+                      f"{one['steps']} steps in {one['seconds']:.1f} s"}
+
+
+_REF_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import lbm_cases as C
+from oracle import Oracle
+import bench
+case = bench.cpu_sample_case({nx})
+o = Oracle(case, *C.initial_fields(case))
+for _ in range({warmup}):
+    o.step()
+t0 = time.perf_counter()
+for _ in range({steps}):
+    o.step()
+dt = time.perf_counter() - t0
+print(json.dumps(dict(steps={steps}, seconds=dt, cells=case.cells)))
+"""
 
 
 def run_reference(args):
+    """The FP64 oracle as it stands on the host cores: one single-threaded copy
+    per core, each running --warmup untimed and --steps timed steps (times
+    --ref-steps-per-step) on its own crop of the workload; value = cells x steps
+    summed over the copies / the longest timed run."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     # crop sized so that the whole run stays within a few minutes
     nx = max(4, min(64, int(64 * 200 / max(args.steps, 1)) // 4 * 4))
-    case = cpu_sample_case(nx)
-    from oracle import Oracle
-    o = Oracle(case, *C.initial_fields(case))
-    for _ in range(max(args.warmup, 0)):
-        o.step()
     per_step = max(1, int(args.ref_steps_per_step))
-    t0 = time.perf_counter()
-    for _ in range(args.steps * per_step):
-        o.step()
-    dt = time.perf_counter() - t0
-    value = case.cells * args.steps * per_step / dt / 1e6
+    n = host_cores()
+    code = _REF_SNIPPET.format(root=ROOT, nx=nx, warmup=max(args.warmup, 0),
+                               steps=args.steps * per_step)
+    res = _oracle_workers(code, n)
+    dt = max(d["seconds"] for d in res)
+    value = sum(d["cells"] * d["steps"] for d in res) / dt / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "channel_3d_D3Q19_256x128x128_fp32_Re5200_slip_bounce_back",
-                       "sample": f"{nx}x128x8 crop of the workload, FP64 oracle"},
-            "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1,
+            "config": {"workload": "channel_3d_D3Q19_256x128x128_fp32_Re5200_slip_bounce_back_yu",
+                       "sample": f"{nx}x128x8 crop of the workload per host core, FP64 oracle"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": n,
                              "kind": "oracle",
-                             "sample": f"{nx}x128x8 crop, {per_step} oracle step(s) per timed step"},
+                             "sample": f"{n} single-threaded oracle copies, each on a {nx}x128x8 "
+                                       f"crop, {per_step} oracle step(s) per timed step"},
             "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -446,8 +505,8 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

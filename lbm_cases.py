@@ -87,7 +87,8 @@ class Case:
     u_init: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # m/s
     perturb: float = 0.0              # relative amplitude of the seeded u_x perturbation
     seed: int = 0
-    nut_ratio_init: float = 3.0       # initial nu_tilde / nu
+    nut_ratio_init: float = 3.0       # initial nu_tilde / nu (floor of the log-layer profile)
+    nut_utau: float = 0.0             # m/s; > 0: initial nu_tilde = max(ratio nu, kappa u_tau d)
     steps: int = 100
     u_shift: Optional[float] = None   # storage reference velocity (None: u_init x)
 
@@ -131,6 +132,18 @@ def initial_fields(case: Case):
         r = rng.uniform(-1.0, 1.0, size=shape)
         u[0] = case.u_init[0] * (1.0 + case.perturb * r)
     nut = np.full(shape, case.nut_ratio_init * case.nu, dtype=np.float64)
+    if case.nut_utau > 0.0:
+        # log-layer start: nu_tilde = kappa u_tau d with d the distance to the
+        # nearest wall face (boundary nodes d_w Delta from their wall)
+        j = np.arange(case.ny, dtype=np.float64)
+        d = np.full(case.ny, np.inf)
+        for f, dist in (("ymin", j), ("ymax", case.ny - 1 - j)):
+            b = case.bcs[f]
+            if b.kind in ("wall_bb", "wall_hrfd", "wall_cai_degrigny"):
+                d = np.minimum(d, (dist + b.d_w) * case.dx)
+        if np.isfinite(d).all():
+            prof = np.maximum(case.nut_ratio_init * case.nu, case.kappa * case.nut_utau * d)
+            nut[:] = prof[None, :, None]
     return rho, u, nut
 
 
@@ -175,12 +188,16 @@ def channel_3d(re_tau: float = 5200.0, scheme: str = "wall_bb", nx: int = 256,
                ny: int = 128, nz: int = 128, seed: int = 0, storage: str = "fp32",
                collision: str = "bgk", wall_law: str = "sa_analytic",
                ref_node: int = 2, steps: int = 1000, d_w: float = 0.5,
-               interp: str = "none") -> Case:
+               interp: str = "none", nut_init: str = "log_layer") -> Case:
     """3-D D3Q19 full channel: walls at y = 0 and y = 2h, periodic in x and z.
 
     The boundary nodes lie d_w Delta from the walls (Section 4.1.2.5; d_w = 1/2
     is the half-way placement), so 2h = (ny - 1 + 2 d_w) Delta; initial
-    u_x = U_b (1 +/- 1 %) seeded; nu_tilde = 3 nu.
+    u_x = U_b (1 +/- 1 %) seeded.  Initial nu_tilde: "log_layer" (default)
+    max(3 nu, kappa u_tau d), the log-layer solution of the SA model with d the
+    wall distance, or "uniform" 3 nu.  (With the uniform start the BGK channel
+    at Re_tau = 5200 on 128 cells begins almost inviscid, tau - 1/2 ~ 1e-4, and
+    diverges within ~2000 steps.)
     """
     h = 1.0
     p = channel_parameters(re_tau, h)
@@ -193,7 +210,7 @@ def channel_3d(re_tau: float = 5200.0, scheme: str = "wall_bb", nx: int = 256,
         collision=collision, storage=storage, turbulence="sa", wall_law=wall_law,
         bcs={"ymin": wall, "ymax": dataclasses.replace(wall)},
         u_init=(p["u_b"], 0.0, 0.0), perturb=0.01, seed=seed, nut_ratio_init=3.0,
-        steps=steps)
+        nut_utau=p["u_tau"] if nut_init == "log_layer" else 0.0, steps=steps)
 
 
 # ----------------------------------------------------------------------------
@@ -204,14 +221,18 @@ def flat_plate_3d(nx: int = 2048, ny: int = 512, nz: int = 8, dx: float = 1e-3,
                   scheme: str = "wall_bb", storage: str = "fp32",
                   collision: str = "regularized", top: str = "freestream",
                   x_inlet: float = -0.2, steps: int = 1000,
-                  u_inf: float = PLATE_U_INF) -> Case:
+                  u_inf: float = PLATE_U_INF, interp: Optional[str] = None) -> Case:
     """3-D D3Q19 flat plate: Zou-He inlet, zero-gradient outlet, free-stream top,
     bottom symmetry for x < 0 and wall for x >= 0, spanwise periodic.
-    Initial state: uniform U_inf with nu_tilde / nu = 3."""
+    Initial state: uniform U_inf with nu_tilde / nu = 3.  A bounce-back wall
+    uses Yu's rule (Eq. 37) by default, as the paper does on the plate
+    (Section 3.2); interp="none" selects half-way bounce-back."""
+    if interp is None:
+        interp = "yu" if scheme == "wall_bb" else "none"
     bcs = {
         "xmin": BC("inlet_zouhe", u_in=(u_inf, 0.0, 0.0), nut_ratio_in=3.0),
         "xmax": BC("outlet_zerograd"),
-        "ymin": BC(scheme, ref_node=2, x_start=0.0),
+        "ymin": BC(scheme, ref_node=2, x_start=0.0, interp=interp),
         "ymax": BC(top, u_in=(u_inf, 0.0, 0.0), nut_ratio_in=3.0),
     }
     return Case(

@@ -113,6 +113,9 @@ __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float pow_sixth(float x) { return __powf(x, 1.0f / 6.0f); }
 __device__ __forceinline__ double pow_sixth(double x) { return pow(x, 1.0 / 6.0); }
+// square root of a non-negative value: x * rsqrt(x) (2 ulp) in FP32, exact in FP64
+__device__ __forceinline__ float nn_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ double nn_sqrt(double x) { return sqrt(x); }
 
 // --------------------------------------------------------------------------
 // Kernel parameters (lattice units), passed by value.
@@ -204,7 +207,7 @@ template <class R> __device__ __forceinline__ R sa_source(R nt, R S, R nu, R inv
   const R c3 = chi * chi * chi;
   const R fv1 = fdiv(c3, c3 + (R)(SAConst::cv1 * SAConst::cv1 * SAConst::cv1));
   const R fv2 = (R)1 - fdiv(chi, (R)1 + chi * fv1);
-  const R inv_kd2 = inv_d2 / (kap * kap);
+  const R inv_kd2 = inv_d2 * ((R)1 / (kap * kap));
   const R sbar = nt * fv2 * inv_kd2;
   R st;
   if (sbar >= -(R)SAConst::cv2lim * S) {
@@ -329,7 +332,7 @@ __device__ R sa_update(const Params& p, const R* __restrict__ nt, const R* __res
   const R wx = h * (pl[1].u[2] - m[1].u[2]) - h * (pl[2].u[1] - m[2].u[1]);
   const R wy = h * (pl[2].u[0] - m[2].u[0]) - h * (pl[0].u[2] - m[0].u[2]);
   const R wz = h * (pl[0].u[1] - m[0].u[1]) - h * (pl[1].u[0] - m[1].u[0]);
-  const R S = sqrt(wx * wx + wy * wy + wz * wz);
+  const R S = nn_sqrt(wx * wx + wy * wy + wz * wz);
   R conv = 0, diff = 0, grad2 = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -377,7 +380,7 @@ __device__ __forceinline__ R sa_update_interior(const Params& p, const R* __rest
     ntm[2] = c;
     ntp[2] = c;
   }
-  const R S = sqrt(S2);
+  const R S = nn_sqrt(S2);
   const R ua[3] = {ux, uy, uz};
   R conv = 0, diff = 0, grad2 = 0;
 #pragma unroll
@@ -591,7 +594,7 @@ __device__ typename Compute<ST>::R pull_bc(const Params& p, int x, int y, int z,
 //   force prefactor 1 - omega/2 = delta / 2.
 // --------------------------------------------------------------------------
 template <class R> __device__ __forceinline__ R relax_delta(R eps) {
-  return (R)4 * eps / ((R)1 + (R)2 * eps);
+  return fdiv((R)4 * eps, (R)1 + (R)2 * eps);
 }
 
 template <int Q, class R>

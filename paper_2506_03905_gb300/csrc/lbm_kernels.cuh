@@ -117,7 +117,8 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
 #endif
 
 // A bounce-back wall node on a lattice with periodic x: the sources of the
-// directions leaving the wall are replaced by Eq. 31, every other source is
+// directions leaving the wall are replaced by the face's rule (Eq. 31, or
+// Eqs. 36-37 through the affine weights of Params::ibb), every other source is
 // in the lattice; nu_tilde is the Dirichlet value the wall pass stored.
 template <int Q, int ST>
 __device__ __forceinline__ void bulk_wall_bb(const Params& p, int fi, int x, int y, int z) {
@@ -135,15 +136,29 @@ __device__ __forceinline__ void bulk_wall_bb(const Params& p, int fi, int x, int
   const R rw = ((const R*)p.rhow[fi])[node];
   const R rux = rw * uw[0], ruy = rw * uw[1], ruz = rw * uw[2];
   const R U = psel<R>(p.Ush, p.Ush_f);
+  const bool interp = p.interp[fi] != 0;
+  const R a0 = psel<R>(p.ibb[fi][0], p.ibb_f[fi][0]), aF = psel<R>(p.ibb[fi][1], p.ibb_f[fi][1]),
+          ai = psel<R>(p.ibb[fi][2], p.ibb_f[fi][2]), aK = psel<R>(p.ibb[fi][3], p.ibb_f[fi][3]);
   R g[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
     const bool from_wall = fi == 0 ? cy > 0 : cy < 0;
     if (from_wall) {
-      // Eq. 31 in deviations: h*_{opp i}(B) + 6 w (rho_w c_i.u_w - c_x U)
+      // Eq. 31 in deviations: h*_{opp i}(B) + K, K = 6 w (rho_w c_i.u_w - c_x U)
       const R cu = (R)cx * rux + (R)cy * ruy + (R)cz * ruz;
-      g[i] = (R)C::ld(fs + (opp(i) * o.nc + o.id)) + (R)6 * (R)L::w(i) * (cu - (R)cx * U);
+      const R K = (R)6 * (R)L::w(i) * (cu - (R)cx * U);
+      const R hoB = (R)C::ld(fs + (opp(i) * o.nc + o.id));
+      if (interp) {
+        // Eqs. 36-37: h*_opp at F = B + c_i (one link into the fluid) and h*_i(B)
+        const int offF = (cx > 0 ? o.oxp : (cx < 0 ? o.oxm : 0)) + (cy > 0 ? o.oyp : o.oym) +
+                         (cz > 0 ? o.ozp : (cz < 0 ? o.ozm : 0));
+        const R hoF = (R)C::ld(fs + (opp(i) * o.nc + o.id + offF));
+        const R hiB = (R)C::ld(fs + (i * o.nc + o.id));
+        g[i] = a0 * hoB + aF * hoF + ai * hiB + aK * K;
+      } else {
+        g[i] = hoB + K;
+      }
     } else {
       const int off = (cx > 0 ? o.oxm : (cx < 0 ? o.oxp : 0)) + (cy > 0 ? o.oym : (cy < 0 ? o.oyp : 0)) +
                       (cz > 0 ? o.ozm : (cz < 0 ? o.ozp : 0));
@@ -174,10 +189,9 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
     return;
   }
   if (p.px && p.turbulent && p.ny >= 3) {
-    // half-way slip bounce-back rows (the interpolated rules take the general path)
-    const int fw = (y == 0 && p.wall[0] == BC_WALL_BB && p.interp[0] == 0 && x >= p.xw0[0]) ? 0
-                 : ((y == p.ny - 1 && p.wall[1] == BC_WALL_BB && p.interp[1] == 0 &&
-                     x >= p.xw0[1]) ? 1 : -1);
+    // slip bounce-back rows (half-way or interpolated)
+    const int fw = (y == 0 && p.wall[0] == BC_WALL_BB && x >= p.xw0[0]) ? 0
+                 : ((y == p.ny - 1 && p.wall[1] == BC_WALL_BB && x >= p.xw0[1]) ? 1 : -1);
     if (fw >= 0) {
       bulk_wall_bb<Q, ST>(p, fw, x, y, z);
       return;
