@@ -273,3 +273,13 @@ def test_kernel_launch_count():
         s.close()
         assert n0 >= 1
         assert (n1 - n0, n2 - n1) == (7 * per_step, 4 * per_step)
+
+
+@pytest.mark.parametrize("scheme,interp", [("wall_bb", "none"), ("wall_bb", "yu"),
+                                           ("wall_hrfd", "none"), ("wall_cai_degrigny", "none")])
+@pytest.mark.parametrize("nsteps", [1, 10, 1000])
+def test_channel_step_counts(scheme, interp, nsteps):
+    """FP32 against the FP64 oracle after 1, 10 and 1000 steps (3-D channel,
+    Re_tau = 5200, 36 x 24 x 4 with ragged 32 x 8 tiles)."""
+    case = C.channel_3d(re_tau=5200.0, scheme=scheme, interp=interp, nx=36, ny=24, nz=4, seed=9)
+    compare(case, nsteps, TOL["fp32"])
