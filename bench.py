@@ -338,7 +338,7 @@ def batched_variant(pkg, torch, steps, rank=0, world=1, storage="fp32"):
     out = {}
     # per-case sequential runs (each graph-replayed)
     for s in solvers:
-        s.step(2)
+        s.step(steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in solvers:
@@ -349,7 +349,9 @@ def batched_variant(pkg, torch, steps, rank=0, world=1, storage="fp32"):
                                   "instances": len(cases), "cells": total}
     b = pkg.lbm_batch_create([s.ctx for s in solvers])
     try:
-        pkg.lbm_batch_step(b, 2)
+        # the first call autotunes; a call with a new step count captures its
+        # graph: both happen before the timed call
+        pkg.lbm_batch_step(b, steps)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pkg.lbm_batch_step(b, steps)

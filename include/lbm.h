@@ -260,11 +260,14 @@ lbm_status lbm_moments_noalloc(const void* f, int lattice, int storage, int nx, 
 typedef struct lbm_batch lbm_batch;
 
 lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** out);
-/* Advance every instance by nsteps; tiles_per_cta and threads are chosen by
-   the built-in autotuner on the first call unless lbm_batch_tune fixed them. */
+/* Advance every instance by nsteps; the tile size (cells per work item, one
+   warp each) and threads per CTA are chosen by the built-in autotuner on the
+   first call unless lbm_batch_tune fixed them.  The autotuner advances every
+   instance while it times (24 steps). */
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
-/* Time the candidate tile sizes / block sizes once and keep the fastest;
-   best[0] = threads per CTA, best[1] = cells per tile. */
+/* Time the candidate tile sizes (64, 256, 1024 cells per warp item) and block
+   sizes (128, 256 threads) once and keep the fastest; best[0] = threads per
+   CTA, best[1] = cells per tile. */
 lbm_status lbm_batch_tune(lbm_batch* b, int best[2]);
 void lbm_batch_destroy(lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);

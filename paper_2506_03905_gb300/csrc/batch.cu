@@ -3,8 +3,8 @@
 //
 // Work is split into items: phase A items are chunks of wall nodes of one y
 // face of one instance, phase B items are ranges of cells of one instance.
-// Every CTA of the persistent grid walks the item lists with a stride of the
-// grid size; a grid barrier separates phase A (wall pre-pass of every
+// Every warp of the persistent grid walks the item lists with a stride of the
+// number of warps in the grid; a grid barrier separates phase A (wall pre-pass of every
 // instance) from phase B (bulk update of every instance) and one step from
 // the next.  The barrier is an atomic counter with a generation number; its
 // spin is bounded (about a second), after which it records LBM_ETIMEOUT and
@@ -85,26 +85,29 @@ __device__ bool grid_sync(GridBar* bar) {
   return ok_sh != 0;
 }
 
-// The parameters of the instance a CTA works on, copied from global memory into
-// shared memory once per work item: read through a reference to global memory
-// every field would be a load, repeated after each population store (which
-// may alias it as far as the compiler knows).
-__device__ __forceinline__ void load_params(Params* dst, const Params* src, int* q_dst,
-                                            const int* q_src) {
-  __syncthreads();   // every thread is done with the previous item's copy
+// Work items are taken by warps: each warp copies the parameters of its
+// item's instance from global memory into its own shared-memory slot (read
+// through a reference to global memory every field would be a load, repeated
+// after each population store, which may alias it as far as the compiler
+// knows).  Warp-private slots need only warp-level synchronisation, so a slow
+// item holds up no other warp of the CTA.
+constexpr int kMaxWarps = 8;   // blocks of at most 256 threads
+
+__device__ __forceinline__ void warp_load_params(Params* dst, const Params* src, int* q_dst,
+                                                 const int* q_src, int lane) {
   static_assert(sizeof(Params) % sizeof(int) == 0, "Params is copied as ints");
+  __syncwarp();      // the warp is done with its previous item's copy
   const int* s = reinterpret_cast<const int*>(src);
   int* d = reinterpret_cast<int*>(dst);
-  for (int k = threadIdx.x; k < (int)(sizeof(Params) / sizeof(int)); k += blockDim.x) d[k] = s[k];
-  if (threadIdx.x == 0) *q_dst = *q_src;
-  __syncthreads();
+  for (int k = lane; k < (int)(sizeof(Params) / sizeof(int)); k += 32) d[k] = s[k];
+  if (lane == 0) *q_dst = *q_src;
+  __syncwarp();
 }
 
 // Minimum resident blocks per SM requested from the compiler for k_batch (its
 // register budget; 0 leaves the choice to the compiler).  Three blocks of 256
 // (<= 80 registers, a few spilled) measured fastest on GB300 for the 96-instance
-// sweep: 10.15 GLUPS against 9.35 with the compiler's 98 registers and 9.37 with
-// two blocks.
+// sweep.
 #ifndef LBM_BATCH_MINB
 #define LBM_BATCH_MINB 3
 #endif
@@ -117,30 +120,32 @@ __device__ __forceinline__ void load_params(Params* dst, const Params* src, int*
 template <int ST>
 __global__ void LBM_BATCH_BOUNDS k_batch(BatchInst* inst, int ninst, const WorkItem* itemsA,
                                int nA, const WorkItem* itemsB, int nB, GridBar* bar, int nsteps) {
-  __shared__ Params sp;
-  __shared__ int sq;
+  __shared__ Params sp[kMaxWarps];
+  __shared__ int sq[kMaxWarps];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib, nw = gridDim.x * (blockDim.x >> 5);
   for (int step = 0; step < nsteps; ++step) {
-    // phase A: wall pre-pass of every instance
-    for (int it = blockIdx.x; it < nA; it += gridDim.x) {
+    // phase A: wall pre-pass of every instance (items of 32 wall nodes)
+    for (int it = gw; it < nA; it += nw) {
       const WorkItem w = itemsA[it];
       const BatchInst& b = inst[w.inst];
-      load_params(&sp, &b.p[(b.cur + step) & 1], &sq, &b.Q);
-      const Params& p = sp;
-      const int Q = sq;
-      for (int node = w.begin + threadIdx.x; node < w.end; node += blockDim.x) {
+      warp_load_params(&sp[wib], &b.p[(b.cur + step) & 1], &sq[wib], &b.Q, lane);
+      const Params& p = sp[wib];
+      const int Q = sq[wib];
+      for (int node = w.begin + lane; node < w.end; node += 32) {
         if (Q == 19) wall_node<19, ST>(p, w.face, node);
         else wall_node<9, ST>(p, w.face, node);
       }
     }
     if (!grid_sync(bar)) return;
     // phase B: bulk update of every cell of every instance
-    for (int it = blockIdx.x; it < nB; it += gridDim.x) {
+    for (int it = gw; it < nB; it += nw) {
       const WorkItem w = itemsB[it];
       const BatchInst& b = inst[w.inst];
-      load_params(&sp, &b.p[(b.cur + step) & 1], &sq, &b.Q);
-      const Params& p = sp;
-      const int Q = sq, nx = p.nx, nxy = p.nx * p.ny;
-      for (int c = w.begin + threadIdx.x; c < w.end; c += blockDim.x) {
+      warp_load_params(&sp[wib], &b.p[(b.cur + step) & 1], &sq[wib], &b.Q, lane);
+      const Params& p = sp[wib];
+      const int Q = sq[wib], nx = p.nx, nxy = p.nx * p.ny;
+      for (int c = w.begin + lane; c < w.end; c += 32) {
         const int z = c / nxy, r = c - z * nxy;
         const int y = r / nx, x = r - y * nx;
         if (Q == 19) bulk_cell<19, ST, true>(p, x, y, z);
@@ -181,7 +186,7 @@ struct lbm_batch {
   WorkItem* d_itemsB = nullptr;
   int nB = 0;
   int threads = 256;
-  int tile = 1024;        // cells per phase-B item
+  int tile = 256;         // cells per phase-B item (one warp each)
   int grid = 0;
   bool tuned = false;
   bool launched = false;  // a launch may still be running: check its barrier flag first
@@ -201,9 +206,20 @@ struct lbm_batch {
     }                                                                        \
   } while (0)
 
+// Instances in work-item order: D3Q19 first, then D2Q9, so that the warps of
+// an SM mostly run one lattice's code at a time (instruction-cache locality).
+static std::vector<int> instance_order(const lbm_batch* b) {
+  std::vector<int> order;
+  for (int q : {19, 9})
+    for (int i = 0; i < (int)b->ctxs.size(); ++i)
+      if (b->ctxs[i]->Q == q) order.push_back(i);
+  return order;
+}
+
+// Phase B items: ranges of `tile` cells of one instance, each advanced by one warp.
 static lbm_status build_items_B(lbm_batch* b, int tile) {
   std::vector<WorkItem> items;
-  for (int i = 0; i < (int)b->ctxs.size(); ++i) {
+  for (int i : instance_order(b)) {
     const lbm_ctx* c = b->ctxs[i];
     const int n = (int)c->ncells;
     for (int a = 0; a < n; a += tile) items.push_back({i, 0, a, std::min(n, a + tile)});
@@ -222,10 +238,10 @@ static lbm_status build_items_B(lbm_batch* b, int tile) {
   return LBM_OK;
 }
 
-// Phase A items: chunks of one block of wall nodes of one face of one instance.
+// Phase A items: chunks of one warp of wall nodes of one face of one instance.
 static lbm_status build_items_A(lbm_batch* b, int chunk) {
   std::vector<WorkItem> items;
-  for (int i = 0; i < (int)b->ctxs.size(); ++i) {
+  for (int i : instance_order(b)) {
     const lbm_ctx* c = b->ctxs[i];
     for (int f = 0; f < 2; ++f) {
       if (!c->base.wall[f]) continue;
@@ -253,7 +269,7 @@ static lbm_status set_threads(lbm_batch* b, int threads) {
   }
   b->threads = threads;
   b->grid = sms * per_sm;
-  lbm_status s = build_items_A(b, threads);
+  lbm_status s = build_items_A(b, 32);
   if (s != LBM_OK) return s;
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
@@ -374,7 +390,7 @@ extern "C" lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** 
     return LBM_ECUDA;
   }
   st = set_threads(b, 256);
-  if (st == LBM_OK) st = build_items_B(b, 1024);
+  if (st == LBM_OK) st = build_items_B(b, 256);
   if (st != LBM_OK) {
     g_batch_err = b->err;
     lbm_batch_destroy(b);
@@ -393,7 +409,7 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int best[2]) {
     if (s0 != LBM_OK) return s0;
   }
   const int threads_c[2] = {128, 256};
-  const int tiles_c[3] = {1, 4, 16};   // multiples of the block size
+  const int tiles_c[3] = {64, 256, 1024};   // cells per warp item
   float best_ms = 1e30f;
   int bt = b->threads, btile = b->tile;
   cudaEvent_t e0, e1;
@@ -404,7 +420,7 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int best[2]) {
     lbm_status s = set_threads(b, t);
     if (s != LBM_OK) continue;
     for (int k : tiles_c) {
-      s = build_items_B(b, t * k);
+      s = build_items_B(b, k);
       if (s != LBM_OK) return s;
       s = launch(b, 1, b->stream);   // warm-up
       if (s != LBM_OK) return s;
@@ -420,7 +436,7 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int best[2]) {
       if (ms < best_ms) {
         best_ms = ms;
         bt = t;
-        btile = t * k;
+        btile = k;
       }
     }
   }

@@ -60,7 +60,7 @@ def test_batch_matches_single_instances_and_oracle():
     batch_s = solvers(cases)
     b = pkg.lbm_batch_create([s.ctx for s in batch_s])
     threads, tile = pkg.lbm_batch_tune(b)          # tuning advances every instance
-    assert threads in (128, 256) and tile % threads == 0
+    assert threads in (128, 256) and tile in (64, 256, 1024)   # cells per warp item
     pkg.lbm_batch_step(b, nsteps - TUNE_STEPS - 5)
     pkg.lbm_batch_step(b, 5)
     got = [s.fields(FIELDS) for s in batch_s]
