@@ -504,6 +504,32 @@ def run_profile_case(args):
                       "bulk_ms": bulk / args.steps, "wall_ms": wall / args.steps}))
 
 
+def run_profile_batch(args):
+    """Short run of the 96-instance batched sweep for profilers: set-up and
+    autotuning, one warm-up launch of 3 steps, then one launch of --steps
+    steps."""
+    import torch
+    import paper_2506_03905_gb300 as pkg
+    cases = C.batched_sweep(96, storage=args.storage)
+    solvers = []
+    for c in cases:
+        s = pkg.Solver(c)
+        s.set_fields(*C.initial_fields(c))
+        solvers.append(s)
+    b = pkg.lbm_batch_create([s.ctx for s in solvers])
+    try:
+        pkg.lbm_batch_step(b, 3)
+        torch.cuda.synchronize()
+        pkg.lbm_batch_step(b, args.steps)
+        torch.cuda.synchronize()
+    finally:
+        pkg.lbm_batch_destroy(b)
+        for s in solvers:
+            s.close()
+    print(json.dumps({"profile_batch": len(cases), "cells": sum(c.cells for c in cases),
+                      "storage": args.storage, "steps": args.steps}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,6 +540,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-steps-per-step", type=int, default=1)
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="short run of the 96-instance batched sweep (for ncu)")
     ap.add_argument("--profile-case", action="store_true",
                     help="short per-launch run of one channel case (for ncu)")
     ap.add_argument("--nx", type=int, default=256)
@@ -524,6 +552,9 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.profile_batch:
+        run_profile_batch(args)
         return
     if args.warmup < 3:
         args.warmup = 3
