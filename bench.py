@@ -255,6 +255,7 @@ def run_ours(args):
     if world == 1 and not args.no_variants:
         vsteps = max(10, min(args.steps, 100))
         for label, kw in [("fp32_hrfd", dict(scheme="wall_hrfd", storage="fp32")),
+                          ("fp32_cai", dict(scheme="wall_cai_degrigny", storage="fp32")),
                           ("fp16_bb", dict(storage="fp16")), ("bf16_bb", dict(storage="bf16")),
                           ("fp16_hrfd", dict(scheme="wall_hrfd", storage="fp16"))]:
             wk = dict(WORKLOAD)
