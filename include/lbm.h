@@ -203,8 +203,9 @@ lbm_status lbm_run_to_convergence(lbm_ctx* ctx, double tol, int check_every, lon
                                   long long* steps_done, double* residual);
 
 /* Raw state for checkpointing: the post-collision populations in storage
-   precision (bytes reported by lbm_state_bytes), the stored velocity and
-   nu_tilde in compute precision and u_tau in FP64, concatenated.  dst and src
+   precision (bytes reported by lbm_state_bytes), the per-cell records of
+   velocity and nu_tilde (u_x, u_y, u_z, nu_tilde) in compute precision and
+   u_tau in FP64, concatenated.  dst and src
    are host buffers of lbm_state_bytes(ctx) bytes. */
 size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_get_state(lbm_ctx* ctx, void* dst);

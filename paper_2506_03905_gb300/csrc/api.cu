@@ -208,14 +208,13 @@ extern "C" lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
   bool ok = true;
   for (int b = 0; b < 2; ++b) {
     c->f[b] = dalloc(c, (size_t)c->Q * c->ncell * c->esz);
-    c->u[b] = dalloc(c, (size_t)3 * c->ncell * c->rsz);
-    c->nt[b] = dalloc(c, (size_t)c->ncell * c->rsz);
+    c->v[b] = dalloc(c, (size_t)4 * c->ncell * c->rsz);
     const size_t nodes = (size_t)k.nx * k.nz;
     c->utau[b] = (double*)dalloc(c, nodes * sizeof(double));
     c->uw[b] = dalloc(c, 3 * nodes * c->rsz);
     c->rhow[b] = dalloc(c, nodes * c->rsz);
     c->frec[b] = dalloc(c, (size_t)c->Q * nodes * c->rsz);
-    ok = ok && c->f[b] && c->u[b] && c->nt[b] && c->utau[b] && c->uw[b] && c->rhow[b] && c->frec[b];
+    ok = ok && c->f[b] && c->v[b] && c->utau[b] && c->uw[b] && c->rhow[b] && c->frec[b];
   }
   c->utau_prev = (double*)dalloc(c, 2 * (size_t)k.nx * k.nz * sizeof(double));
   c->flags = (unsigned*)dalloc(c, sizeof(unsigned) * 4);
@@ -442,10 +441,8 @@ Params lbm_ctx_params(const lbm_ctx* c, int src) {
   Params p = c->base;
   p.f_src = c->f[src];
   p.f_dst = c->f[1 - src];
-  p.u_src = c->u[src];
-  p.u_dst = c->u[1 - src];
-  p.nt_src = c->nt[src];
-  p.nt_dst = c->nt[1 - src];
+  p.v_src = c->v[src];
+  p.v_dst = c->v[1 - src];
   return p;
 }
 
@@ -901,13 +898,12 @@ extern "C" lbm_status lbm_get_state(lbm_ctx* c, void* dst) {
     return LBM_EINVAL;
   }
   char* o = (char*)dst;
-  const size_t fb = (size_t)c->Q * c->ncell * c->esz, ub = 3 * (size_t)c->ncell * c->rsz,
-               nb = (size_t)c->ncell * c->rsz, wb = (size_t)c->nx * c->nz * sizeof(double);
+  const size_t fb = (size_t)c->Q * c->ncell * c->esz, vb = 4 * (size_t)c->ncell * c->rsz,
+               wb = (size_t)c->nx * c->nz * sizeof(double);
   CUDA_TRY(c, cudaMemcpyAsync(o, c->f[c->cur], fb, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(o + fb, c->u[c->cur], ub, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(o + fb + ub, c->nt[c->cur], nb, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(o + fb + ub + nb, c->utau[0], wb, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(o + fb + ub + nb + wb, c->utau[1], wb, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(o + fb, c->v[c->cur], vb, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(o + fb + vb, c->utau[0], wb, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(o + fb + vb + wb, c->utau[1], wb, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
@@ -917,13 +913,12 @@ extern "C" lbm_status lbm_set_state(lbm_ctx* c, const void* src) {
   lbm_status s = lbm_ctx_finalize(c);
   if (s != LBM_OK) return s;
   const char* o = (const char*)src;
-  const size_t fb = (size_t)c->Q * c->ncell * c->esz, ub = 3 * (size_t)c->ncell * c->rsz,
-               nb = (size_t)c->ncell * c->rsz, wb = (size_t)c->nx * c->nz * sizeof(double);
+  const size_t fb = (size_t)c->Q * c->ncell * c->esz, vb = 4 * (size_t)c->ncell * c->rsz,
+               wb = (size_t)c->nx * c->nz * sizeof(double);
   CUDA_TRY(c, cudaMemcpyAsync(c->f[c->cur], o, fb, cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c->u[c->cur], o + fb, ub, cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c->nt[c->cur], o + fb + ub, nb, cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c->utau[0], o + fb + ub + nb, wb, cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c->utau[1], o + fb + ub + nb + wb, wb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->v[c->cur], o + fb, vb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->utau[0], o + fb + vb, wb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->utau[1], o + fb + vb + wb, wb, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * 4, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->ready = true;

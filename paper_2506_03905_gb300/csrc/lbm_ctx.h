@@ -25,8 +25,7 @@ struct lbm_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int prio_hi = 0;                     // greatest stream priority of the device
   void* f[2] = {nullptr, nullptr};
-  void* u[2] = {nullptr, nullptr};
-  void* nt[2] = {nullptr, nullptr};
+  void* v[2] = {nullptr, nullptr};   // SA-field records (u_x, u_y, u_z, nu_tilde) per cell
   double* utau[2] = {nullptr, nullptr};
   void* uw[2] = {nullptr, nullptr};
   void* rhow[2] = {nullptr, nullptr};

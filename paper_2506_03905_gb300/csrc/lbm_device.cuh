@@ -9,8 +9,9 @@
 //
 // Memory layout (structure of arrays, x fastest, rows padded to `pitch`):
 //   f[q][z][y][x]  -> f[q * ncell + (z*ny + y)*pitch + x]
-//   u[c][z][y][x]  -> u[c * ncell + ...]      (velocity of the previous step)
-//   nt[z][y][x]                               (SA working variable)
+//   v[z][y][x][4] -> v[4 * ((z*ny + y)*pitch + x) + k]: per cell the record
+//                    (u_x, u_y, u_z, nu_tilde) of the previous step, so that the
+//                    SA stencil reads a neighbour with one vector load
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
@@ -157,10 +158,8 @@ struct Params {
   // state
   const void* f_src;
   void* f_dst;
-  const void* u_src;
-  void* u_dst;
-  const void* nt_src;
-  void* nt_dst;
+  const void* v_src;           // SA-field records (u_x, u_y, u_z, nu_tilde), compute type
+  void* v_dst;
   double* utau[2];             // per wall node, FP64 (also the Newton warm start)
   void* uw[2];                 // BB: slip velocity (3 per node), compute type
   void* rhow[2];               // BB: wall density, compute type
@@ -172,6 +171,33 @@ struct Params {
 template <class R> __device__ __forceinline__ R psel(double d, float f);
 template <> __device__ __forceinline__ float psel<float>(double, float f) { return f; }
 template <> __device__ __forceinline__ double psel<double>(double d, float) { return d; }
+
+// SA-field record of a cell: the velocity and nu_tilde, stored together (16 B
+// in FP32, 32 B in FP64).  ld_rec reads a record that no thread of the running
+// kernel writes (the source buffer) through the read-only path; st_rec writes
+// one with vector stores.
+template <class R> struct Rec {
+  R x, y, z, n;   // u_x, u_y, u_z, nu_tilde
+};
+template <class I> __device__ __forceinline__ Rec<float> ld_rec(const float* v, I id) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(v) + id);
+  return {a.x, a.y, a.z, a.w};
+}
+template <class I> __device__ __forceinline__ Rec<double> ld_rec(const double* v, I id) {
+  const double2* q = reinterpret_cast<const double2*>(v) + 2 * id;
+  const double2 a = __ldg(q), b = __ldg(q + 1);
+  return {a.x, a.y, b.x, b.y};
+}
+template <class I>
+__device__ __forceinline__ void st_rec(float* v, I id, float x, float y, float z, float n) {
+  reinterpret_cast<float4*>(v)[id] = make_float4(x, y, z, n);
+}
+template <class I>
+__device__ __forceinline__ void st_rec(double* v, I id, double x, double y, double z, double n) {
+  double2* q = reinterpret_cast<double2*>(v) + 2 * id;
+  q[0] = make_double2(x, y);
+  q[1] = make_double2(z, n);
+}
 
 __device__ __forceinline__ long long cidx(const Params& p, int x, int y, int z) {
   return ((long long)z * p.ny + y) * p.pitch + x;
@@ -238,27 +264,27 @@ template <class R> struct Nb {
 };
 
 template <class R>
-__device__ __forceinline__ Nb<R> load_nb(const Params& p, const R* __restrict__ nt,
-                                         const R* __restrict__ u, int x, int y, int z) {
+__device__ __forceinline__ Nb<R> load_nb(const Params& p, const R* __restrict__ v, int x, int y,
+                                         int z) {
+  const Rec<R> r = ld_rec(v, cidx(p, x, y, z));
   Nb<R> n;
-  const long long id = cidx(p, x, y, z);
-  n.nt = nt[id];
-  n.u[0] = u[id];
-  n.u[1] = u[id + p.ncell];
-  n.u[2] = u[id + 2 * p.ncell];
+  n.nt = r.n;
+  n.u[0] = r.x;
+  n.u[1] = r.y;
+  n.u[2] = r.z;
   return n;
 }
 
 template <class R>
-__device__ Nb<R> neighbour(const Params& p, const R* __restrict__ nt, const R* __restrict__ u,
-                           int x, int y, int z, int axis, int s) {
+__device__ Nb<R> neighbour(const Params& p, const R* __restrict__ v, int x, int y, int z,
+                           int axis, int s) {
   if (axis == 0) {
     int xn = x + s;
-    if (xn >= 0 && xn < p.nx) return load_nb<R>(p, nt, u, xn, y, z);
-    if (p.px) return load_nb<R>(p, nt, u, xn < 0 ? xn + p.nx : xn - p.nx, y, z);
+    if (xn >= 0 && xn < p.nx) return load_nb<R>(p, v, xn, y, z);
+    if (p.px) return load_nb<R>(p, v, xn < 0 ? xn + p.nx : xn - p.nx, y, z);
     const int f = xn < 0 ? XMIN : XMAX;
     const int k = p.kind[f];
-    if (k == BC_OUTLET) return load_nb<R>(p, nt, u, x, y, z);
+    if (k == BC_OUTLET) return load_nb<R>(p, v, x, y, z);
     Nb<R> n;  // inlet (and any prescribed face)
     n.nt = psel<R>(p.nt_face[f], p.nt_face_f[f]);
     n.u[0] = psel<R>(p.u_face[f][0], p.u_face_f[f][0]);
@@ -268,8 +294,8 @@ __device__ Nb<R> neighbour(const Params& p, const R* __restrict__ nt, const R* _
   }
   if (axis == 1) {
     int yn = y + s;
-    if (yn >= 0 && yn < p.ny) return load_nb<R>(p, nt, u, x, yn, z);
-    if (p.py) return load_nb<R>(p, nt, u, x, yn < 0 ? yn + p.ny : yn - p.ny, z);
+    if (yn >= 0 && yn < p.ny) return load_nb<R>(p, v, x, yn, z);
+    if (p.py) return load_nb<R>(p, v, x, yn < 0 ? yn + p.ny : yn - p.ny, z);
     const int f = yn < 0 ? YMIN : YMAX;
     const int k = p.kind[f];
     if (k == BC_FREESTREAM) {
@@ -280,13 +306,13 @@ __device__ Nb<R> neighbour(const Params& p, const R* __restrict__ nt, const R* _
       n.u[2] = psel<R>(p.u_face[f][2], p.u_face_f[f][2]);
       return n;
     }
-    Nb<R> n = load_nb<R>(p, nt, u, x, y, z);  // mirror
+    Nb<R> n = load_nb<R>(p, v, x, y, z);  // mirror
     n.u[1] = -n.u[1];
     return n;
   }
   int zn = z + s;
   zn = zn < 0 ? zn + p.nz : (zn >= p.nz ? zn - p.nz : zn);
-  return load_nb<R>(p, nt, u, x, y, zn);
+  return load_nb<R>(p, v, x, y, zn);
 }
 
 template <class R> __device__ __forceinline__ R inv_wall_dist2(const Params& p, int x, int y) {
@@ -311,18 +337,17 @@ template <class R> __device__ __forceinline__ R inv_wall_dist2(const Params& p, 
 
 // Explicit Euler update of Eq. 11 at one cell, clipped at zero.
 template <class R, bool THREE_D>
-__device__ R sa_update(const Params& p, const R* __restrict__ nt, const R* __restrict__ u, int x,
-                       int y, int z) {
-  const Nb<R> c = load_nb<R>(p, nt, u, x, y, z);
+__device__ R sa_update(const Params& p, const R* __restrict__ v, int x, int y, int z) {
+  const Nb<R> c = load_nb<R>(p, v, x, y, z);
   const R nu = psel<R>(p.nu, p.nu_f);
   Nb<R> m[3], pl[3];
-  m[0] = neighbour<R>(p, nt, u, x, y, z, 0, -1);
-  pl[0] = neighbour<R>(p, nt, u, x, y, z, 0, +1);
-  m[1] = neighbour<R>(p, nt, u, x, y, z, 1, -1);
-  pl[1] = neighbour<R>(p, nt, u, x, y, z, 1, +1);
+  m[0] = neighbour<R>(p, v, x, y, z, 0, -1);
+  pl[0] = neighbour<R>(p, v, x, y, z, 0, +1);
+  m[1] = neighbour<R>(p, v, x, y, z, 1, -1);
+  pl[1] = neighbour<R>(p, v, x, y, z, 1, +1);
   if (THREE_D) {
-    m[2] = neighbour<R>(p, nt, u, x, y, z, 2, -1);
-    pl[2] = neighbour<R>(p, nt, u, x, y, z, 2, +1);
+    m[2] = neighbour<R>(p, v, x, y, z, 2, -1);
+    pl[2] = neighbour<R>(p, v, x, y, z, 2, +1);
   } else {
     m[2] = c;
     pl[2] = c;
@@ -351,30 +376,34 @@ __device__ R sa_update(const Params& p, const R* __restrict__ nt, const R* __res
 }
 
 // Same update for a cell whose six neighbours are all inside the lattice
-// (periodic z handled by the plane offsets ozm / ozp); no ghost logic.
+// (periodic z handled by the plane offsets ozm / ozp); no ghost logic.  One
+// record load per neighbour: x neighbours give nu_tilde, u_y, u_z; y
+// neighbours nu_tilde, u_x, u_z; z neighbours nu_tilde, u_x, u_y.
 template <class R, bool THREE_D>
-__device__ __forceinline__ R sa_update_interior(const Params& p, const R* __restrict__ nt,
-                                                const R* __restrict__ u, int id, int nc, int oxm,
-                                                int oxp, int oym, int oyp, int ozm, int ozp, int x,
-                                                int y) {
+__device__ __forceinline__ R sa_update_interior(const Params& p, const R* __restrict__ v, int id,
+                                                int oxm, int oxp, int oym, int oyp, int ozm,
+                                                int ozp, int x, int y) {
   const R nu = psel<R>(p.nu, p.nu_f);
   const R h = (R)0.5;
-  const R c = nt[id];
+  const Rec<R> cc = ld_rec(v, id);
+  const Rec<R> xm = ld_rec(v, id + oxm), xp = ld_rec(v, id + oxp);
+  const Rec<R> ym = ld_rec(v, id + oym), yp = ld_rec(v, id + oyp);
+  const R c = cc.n;
   R ntm[3], ntp[3];
-  ntm[0] = nt[id + oxm];
-  ntp[0] = nt[id + oxp];
-  ntm[1] = nt[id + oym];
-  ntp[1] = nt[id + oyp];
-  const R ux = u[id], uy = u[id + nc], uz = THREE_D ? u[id + 2 * nc] : (R)0;
+  ntm[0] = xm.n;
+  ntp[0] = xp.n;
+  ntm[1] = ym.n;
+  ntp[1] = yp.n;
+  const R ux = cc.x, uy = cc.y, uz = THREE_D ? cc.z : (R)0;
   // vorticity by central differences of the previous-step velocity
-  R wz = h * ((u[nc + id + oxp] - u[nc + id + oxm]) - (u[id + oyp] - u[id + oym]));
+  R wz = h * ((xp.y - xm.y) - (yp.x - ym.x));
   R S2 = wz * wz;
   if (THREE_D) {
-    ntm[2] = nt[id + ozm];
-    ntp[2] = nt[id + ozp];
-    const R wx = h * ((u[2 * nc + id + oyp] - u[2 * nc + id + oym]) -
-                      (u[nc + id + ozp] - u[nc + id + ozm]));
-    const R wy = h * ((u[id + ozp] - u[id + ozm]) - (u[2 * nc + id + oxp] - u[2 * nc + id + oxm]));
+    const Rec<R> zm = ld_rec(v, id + ozm), zp = ld_rec(v, id + ozp);
+    ntm[2] = zm.n;
+    ntp[2] = zp.n;
+    const R wx = h * ((yp.z - ym.z) - (zp.y - zm.y));
+    const R wy = h * ((zp.x - zm.x) - (xp.z - xm.z));
     S2 += wx * wx + wy * wy;
   } else {
     ntm[2] = c;

@@ -50,18 +50,15 @@ __device__ __forceinline__ void interior_finish(const Params& p, const NbOff& o,
   using R = typename Compute<ST>::R;
   using T = typename C::T;
   T* __restrict__ fd = (T*)p.f_dst;
-  const R* __restrict__ us = (const R*)p.u_src;
-  R* __restrict__ ud = (R*)p.u_dst;
-  const R* __restrict__ ns = (const R*)p.nt_src;
-  R* __restrict__ nd = (R*)p.nt_dst;
+  const R* __restrict__ vs = (const R*)p.v_src;
+  R* __restrict__ vd = (R*)p.v_dst;
   // SA working variable of the new step (Eq. 11)
   R ntn;
   if (p.turbulent)
-    ntn = sa_update_interior<R, (Q == 19)>(p, ns, us, o.id, o.nc, o.oxm, o.oxp, o.oym, o.oyp, o.ozm,
-                                            o.ozp, x, y);
+    ntn = sa_update_interior<R, (Q == 19)>(p, vs, o.id, o.oxm, o.oxp, o.oym, o.oyp, o.ozm, o.ozp,
+                                            x, y);
   else
-    ntn = ns[o.id];
-  nd[o.id] = ntn;
+    ntn = vs[4 * o.id + 3];
   const R nu = psel<R>(p.nu, p.nu_f);
   const R nut = p.turbulent ? sa_nut<R>(ntn, nu) : (R)0;
   const R delta = relax_delta<R>((R)3 * (nu + nut));   // 2 - omega (Eq. 8)
@@ -71,9 +68,7 @@ __device__ __forceinline__ void interior_finish(const Params& p, const NbOff& o,
   // store
 #pragma unroll
   for (int i = 0; i < Q; ++i) C::st(fd + (i * o.nc + o.id), g[i]);
-  ud[o.id] = u[0];
-  ud[o.id + o.nc] = u[1];
-  ud[o.id + 2 * o.nc] = u[2];
+  st_rec(vd, o.id, u[0], u[1], u[2], ntn);
 }
 
 template <int Q, int ST>
@@ -128,8 +123,7 @@ __device__ __forceinline__ void bulk_wall_bb(const Params& p, int fi, int x, int
   using T = typename C::T;
   const T* __restrict__ fs = (const T*)p.f_src;
   T* __restrict__ fd = (T*)p.f_dst;
-  R* __restrict__ ud = (R*)p.u_dst;
-  const R* __restrict__ nd = (const R*)p.nt_dst;
+  R* __restrict__ vd = (R*)p.v_dst;
   const NbOff o = nb_offsets(p, x, y, z);
   const int node = z * (p.nx - p.xw0[fi]) + (x - p.xw0[fi]);
   const R* uw = (const R*)p.uw[fi] + 3 * node;
@@ -165,16 +159,16 @@ __device__ __forceinline__ void bulk_wall_bb(const Params& p, int fi, int x, int
       g[i] = (R)C::ld(fs + (i * o.nc + o.id + off));
     }
   }
+  // the Dirichlet nu_tilde_B the wall pass wrote into this step's record
+  const R ntB = vd[4 * o.id + 3];
   const R nu = psel<R>(p.nu, p.nu_f);
-  const R nut = p.turbulent ? sa_nut<R>(nd[o.id], nu) : (R)0;
+  const R nut = p.turbulent ? sa_nut<R>(ntB, nu) : (R)0;
   const R delta = relax_delta<R>((R)3 * (nu + nut));
   R u[3];
   collide<Q, R>(p, g, delta, u);
 #pragma unroll
   for (int i = 0; i < Q; ++i) C::st(fd + (i * o.nc + o.id), g[i]);
-  ud[o.id] = u[0];
-  ud[o.id + o.nc] = u[1];
-  ud[o.id + 2 * o.nc] = u[2];
+  st_rec(vd, o.id, u[0], u[1], u[2], ntB);
 }
 
 // One cell of the bulk update (every cell of the lattice takes this path).
@@ -199,10 +193,8 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
   }
   const long long id = cidx(p, x, y, z);
   T* __restrict__ fd = (T*)p.f_dst;
-  const R* __restrict__ us = (const R*)p.u_src;
-  R* __restrict__ ud = (R*)p.u_dst;
-  const R* __restrict__ ns = (const R*)p.nt_src;
-  R* __restrict__ nd = (R*)p.nt_dst;
+  const R* __restrict__ vs = (const R*)p.v_src;
+  R* __restrict__ vd = (R*)p.v_dst;
 
   int wf = -1;
   if (y == 0 && p.wall[0] && x >= p.xw0[0]) wf = 0;
@@ -213,14 +205,12 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
   R ntn;
   if (p.turbulent) {
     if (wf >= 0) {
-      ntn = nd[id];
+      ntn = vd[4 * id + 3];   // Dirichlet value written by the wall pass
     } else {
-      ntn = inlet ? psel<R>(p.nt_face[XMIN], p.nt_face_f[XMIN]) : sa_update<R, (Q == 19)>(p, ns, us, x, y, z);
-      nd[id] = ntn;
+      ntn = inlet ? psel<R>(p.nt_face[XMIN], p.nt_face_f[XMIN]) : sa_update<R, (Q == 19)>(p, vs, x, y, z);
     }
   } else {
-    ntn = ns[id];
-    nd[id] = ntn;
+    ntn = vs[4 * id + 3];
   }
   const R nu = psel<R>(p.nu, p.nu_f);
   const R nut = p.turbulent ? sa_nut<R>(ntn, nu) : (R)0;
@@ -278,9 +268,7 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
   // 4. store
 #pragma unroll
   for (int i = 0; i < Q; ++i) C::st(fd + i * p.ncell + id, g[i]);
-  ud[id] = u[0];
-  ud[id + p.ncell] = u[1];
-  ud[id + 2 * p.ncell] = u[2];
+  st_rec(vd, id, u[0], u[1], u[2], ntn);
 }
 
 template <int Q, int ST, bool GENERAL>
@@ -454,9 +442,8 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
   const int x = p.xw0[fi] + node % nwx;
   const int yB = fi == 0 ? 0 : p.ny - 1;
   const int s = fi == 0 ? 1 : -1;   // inward direction along y
-  const R* __restrict__ us = (const R*)p.u_src;
-  const R* __restrict__ ns = (const R*)p.nt_src;
-  R* __restrict__ nd = (R*)p.nt_dst;
+  const R* __restrict__ vs = (const R*)p.v_src;
+  R* __restrict__ vd = (R*)p.v_dst;
   const T* __restrict__ fs = (const T*)p.f_src;
   const double nu = p.nu;
   const long long idB = cidx(p, x, yB, z);
@@ -469,7 +456,7 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const double dw = p.d_w[fi];                       // y_B (1/2 half-way)
     const double yref = (double)(p.ref_node[fi] - 1) + dw;
     const long long idR = cidx(p, x, yR, z);
-    const double Ux = (double)us[idR], Uz = (double)us[idR + 2 * p.ncell];
+    const double Ux = (double)vs[4 * idR], Uz = (double)vs[4 * idR + 2];
     const double U = sqrt(Ux * Ux + Uz * Uz);
     const double tx = U > 0.0 ? Ux / U : 1.0, tz = U > 0.0 ? Uz / U : 0.0;
     R* uw = (R*)p.uw[fi] + 3 * node;
@@ -479,10 +466,10 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
       const double nutB = nu * WF::kappa * ypB;
       // Eq. 35 with Delta_w = y_B = d_w and nu_t|_B = nu kappa y_B+
       const double slip = ut * ut * dw / (nu + nutB);
-      uw[0] = (R)((double)us[idB] - slip * tx);
+      uw[0] = (R)((double)vs[4 * idB] - slip * tx);
       uw[1] = (R)0;
-      uw[2] = (R)((double)us[idB + 2 * p.ncell] - slip * tz);
-      nd[idB] = (R)(nu * WF::kappa * ypB);
+      uw[2] = (R)((double)vs[4 * idB + 2] - slip * tz);
+      vd[4 * idB + 3] = (R)(nu * WF::kappa * ypB);
     } else {
       uw[0] = uw[1] = uw[2] = (R)0;
     }
@@ -527,13 +514,13 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const R rhoB = (R)1 + gpar + (R)2 * gperp;
     // velocity gradient G[a][c] = d_a u_c at B from the previous-step velocity
     R G[3][3];
-    const Nb<R> xm = neighbour<R>(p, ns, us, x, yB, z, 0, -1);
-    const Nb<R> xp = neighbour<R>(p, ns, us, x, yB, z, 0, +1);
+    const Nb<R> xm = neighbour<R>(p, vs, x, yB, z, 0, -1);
+    const Nb<R> xp = neighbour<R>(p, vs, x, yB, z, 0, +1);
 #pragma unroll
     for (int c = 0; c < 3; ++c) G[0][c] = (R)0.5 * (xp.u[c] - xm.u[c]);
     if (Q == 19) {
-      const Nb<R> zm = neighbour<R>(p, ns, us, x, yB, z, 2, -1);
-      const Nb<R> zp = neighbour<R>(p, ns, us, x, yB, z, 2, +1);
+      const Nb<R> zm = neighbour<R>(p, vs, x, yB, z, 2, -1);
+      const Nb<R> zp = neighbour<R>(p, vs, x, yB, z, 2, +1);
 #pragma unroll
       for (int c = 0; c < 3; ++c) G[2][c] = (R)0.5 * (zp.u[c] - zm.u[c]);
     } else {
@@ -560,13 +547,13 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const R beta = cai ? (R)1 : (R)p.beta[fi];     // Eq. 30: beta = 1 with Eq. 29
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const R fd = (R)0.5 * ((R)-3 * us[idB + c * p.ncell] + (R)4 * us[idF + c * p.ncell] -
-                             us[idFF + c * p.ncell]);                       // Eq. 28
+      const R fd = (R)0.5 * ((R)-3 * vs[4 * idB + c] + (R)4 * vs[4 * idF + c] -
+                             vs[4 * idFF + c]);                              // Eq. 28
       R dn = fd;
       if (c != 1 && p.turbulent) dn = beta * (R)(ana * tdir[c]) + ((R)1 - beta) * fd;  // Eq. 27
       G[1][c] = (R)s * dn;
     }
-    const R ntB = ns[idB];
+    const R ntB = vs[4 * idB + 3];
     const R nutB = p.turbulent ? sa_nut<R>(ntB, (R)nu) : (R)0;
     const R tau = (R)0.5 + (R)3 * ((R)nu + nutB);
     const R Sxx = G[0][0], Syy = G[1][1], Szz = G[2][2];
@@ -586,7 +573,7 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
                    (R)2 * ((R)(cx * cy) * Sxy + (R)(cx * cz) * Sxz + (R)(cy * cz) * Syz) - trS;
       fr[i] = geq - (R)3 * (R)L::w(i) * rhoB * tau * qs;     // Eqs. 19, 26
     }
-    if (p.turbulent) nd[idB] = (R)(nu * WF::kappa * ypB);
+    if (p.turbulent) vd[4 * idB + 3] = (R)(nu * WF::kappa * ypB);
   }
   p.utau[fi][node] = ut;
   if (!ok) atomicOr(p.flags, FLAG_NEWTON);
@@ -628,11 +615,7 @@ __global__ void k_init(const Params p, const double* rho, const double* u, const
 #pragma unroll
     for (int i = 0; i < Q; ++i)
       C::st((T*)p.f_dst + i * p.ncell + id, heq_dev<Q, R>(i, drho, dux, uy, uz, U, uu15, du15));
-    R* ud = (R*)p.u_dst;
-    ud[id] = ux;
-    ud[id + p.ncell] = uy;
-    ud[id + 2 * p.ncell] = uz;
-    ((R*)p.nt_dst)[id] = (R)(nt[k] * nucv);
+    st_rec((R*)p.v_dst, id, ux, uy, uz, (R)(nt[k] * nucv));
   }
 }
 
@@ -647,8 +630,7 @@ __global__ void k_fields(const Params p, double* rho, double* u, double* nut, do
   using T = typename C::T;
   const long long n = (long long)p.nx * p.ny * p.nz;
   const T* fs = (const T*)p.f_src;
-  const R* us = (const R*)p.u_src;
-  const R* ns = (const R*)p.nt_src;
+  const R* vs = (const R*)p.v_src;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(k % p.nx);
@@ -663,18 +645,19 @@ __global__ void k_fields(const Params p, double* rho, double* u, double* nut, do
       r += gi;
     }
     if (rho) rho[k] = r * rho0;
+    const Rec<R> rec = ld_rec(vs, id);
     if (u) {
-      u[k] = (double)us[id] * vel;
-      u[k + n] = (double)us[id + p.ncell] * vel;
-      u[k + 2 * n] = (double)us[id + 2 * p.ncell] * vel;
+      u[k] = (double)rec.x * vel;
+      u[k + n] = (double)rec.y * vel;
+      u[k + 2 * n] = (double)rec.z * vel;
     }
-    const double ntl = (double)ns[id];
+    const double ntl = (double)rec.n;
     if (nt) nt[k] = ntl * visc;
     if (nut) {
       const double chi = ntl / p.nu, c3 = chi * chi * chi;
       nut[k] = p.turbulent ? ntl * c3 / (c3 + 7.1 * 7.1 * 7.1) * visc : 0.0;
     }
-    fin = fin && isfinite((double)us[id]) && isfinite(ntl);
+    fin = fin && isfinite((double)rec.x) && isfinite(ntl);
     if (!fin) atomicOr(p.flags, FLAG_NONFINITE);
   }
 }
