@@ -217,6 +217,8 @@ extern "C" lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     ok = ok && c->f[b] && c->v[b] && c->utau[b] && c->uw[b] && c->rhow[b] && c->frec[b];
   }
   c->utau_prev = (double*)dalloc(c, 2 * (size_t)k.nx * k.nz * sizeof(double));
+  c->invd2 = dalloc(c, (size_t)c->pitch * k.ny * c->rsz);
+  ok = ok && c->invd2;
   c->flags = (unsigned*)dalloc(c, sizeof(unsigned) * 4);
   c->red_blocks = 2 * 152;
   c->red_chunk = (c->ncells + c->red_blocks - 1) / c->red_blocks;
@@ -417,6 +419,43 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
     p.frec[b] = c->frec[b];
   }
   p.flags = c->flags;
+  // 1 / d^2 of the SA model per (y, x): distance to the nearest wall face (the
+  // line d_w below row 0 / above row ny - 1), measured to the leading-edge
+  // point for columns upstream of a wall's x_start; 0 without walls
+  {
+    std::vector<double> tab((size_t)c->pitch * c->ny, 0.0);
+    for (int y = 0; y < c->ny; ++y)
+      for (int x = 0; x < c->nx; ++x) {
+        double d2 = INFINITY;
+        for (int f = 0; f < 2; ++f) {
+          if (!p.wall[f]) continue;
+          const double dy = f == 0 ? y + p.d_w[f] : (c->ny - 1 - y) + p.d_w[f];
+          double e = dy * dy;
+          if (x < p.xw0[f]) {
+            const double dxl = (x + 0.5) - p.xs_lb[f];
+            e += dxl * dxl;
+          }
+          d2 = std::min(d2, e);
+        }
+        tab[(size_t)y * c->pitch + x] = std::isfinite(d2) ? 1.0 / d2 : 0.0;
+      }
+    // on the context stream, complete before the host copy goes out of scope
+    std::vector<float> tf;
+    const void* src = tab.data();
+    size_t bytes = tab.size() * sizeof(double);
+    if (c->rsz != sizeof(double)) {
+      tf.assign(tab.begin(), tab.end());
+      src = tf.data();
+      bytes = tf.size() * sizeof(float);
+    }
+    cudaError_t e = cudaMemcpyAsync(c->invd2, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      lbm_ctx_set_error(c, "wall-distance table upload failed: %s", cudaGetErrorString(e));
+      return LBM_ECUDA;
+    }
+  }
+  p.invd2 = c->invd2;
   build_tensor_maps(c);
   // float copies of the lattice parameters for the FP32 kernels
   p.nu_f = (float)p.nu;

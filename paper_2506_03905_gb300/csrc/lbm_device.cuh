@@ -164,6 +164,7 @@ struct Params {
   void* uw[2];                 // BB: slip velocity (3 per node), compute type
   void* rhow[2];               // BB: wall density, compute type
   void* frec[2];               // HRFD: rebuilt populations (Q per node), deviations, compute type
+  const void* invd2;           // 1 / d^2 (wall distance of the SA model), compute type, [y][x]
   unsigned* flags;
 };
 
@@ -315,24 +316,13 @@ __device__ Nb<R> neighbour(const Params& p, const R* __restrict__ v, int x, int 
   return load_nb<R>(p, v, x, y, zn);
 }
 
+// 1 / d^2 with d the distance from the cell centre to the nearest wall (0
+// without walls): a wall face is the line d_w below the first (above the
+// last) row, a wall with a leading edge at x_start the half-line x >= x_start,
+// and upstream cells measure to its edge point.  The context tabulates it per
+// (y, x) when its faces are set (lbm_ctx_finalize); the kernels read the table.
 template <class R> __device__ __forceinline__ R inv_wall_dist2(const Params& p, int x, int y) {
-  R d2 = (R)3.0e38;
-  bool any = false;
-#pragma unroll
-  for (int f = 0; f < 2; ++f) {
-    if (p.wall[f]) {
-      const R dw = psel<R>(p.d_w[f], p.d_w_f[f]);
-      const R dy = f == 0 ? (R)y + dw : (R)(p.ny - 1 - y) + dw;
-      R e = dy * dy;
-      if (x < p.xw0[f]) {
-        const R dxl = ((R)x + (R)0.5) - psel<R>(p.xs_lb[f], p.xs_lb_f[f]);
-        e += dxl * dxl;
-      }
-      d2 = e < d2 ? e : d2;
-      any = true;
-    }
-  }
-  return any ? fdiv((R)1, d2) : (R)0;
+  return __ldg((const R*)p.invd2 + (y * p.pitch + x));
 }
 
 // Explicit Euler update of Eq. 11 at one cell, clipped at zero.
