@@ -85,25 +85,40 @@ __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i 
 // stay in the normal range (|g| < 16 is always representable).
 // --------------------------------------------------------------------------
 template <int ST> struct Codec;
+// ld / st convert between storage and deviations in the compute type; the
+// raw forms leave the storage scale kScale in (stored value = kScale x h),
+// for the interior path, whose collision takes the scale into its constants.
 template <> struct Codec<ST_FP32> {
   using T = float;
+  static constexpr int kScale = 1;
   __device__ static __forceinline__ float ld(const T* p) { return *p; }
   __device__ static __forceinline__ void st(T* p, float v) { *p = v; }
+  __device__ static __forceinline__ float ld_raw(const T* p) { return *p; }
+  __device__ static __forceinline__ void st_raw(T* p, float v) { *p = v; }
 };
 template <> struct Codec<ST_FP64> {
   using T = double;
+  static constexpr int kScale = 1;
   __device__ static __forceinline__ double ld(const T* p) { return *p; }
   __device__ static __forceinline__ void st(T* p, double v) { *p = v; }
+  __device__ static __forceinline__ double ld_raw(const T* p) { return *p; }
+  __device__ static __forceinline__ void st_raw(T* p, double v) { *p = v; }
 };
 template <> struct Codec<ST_FP16> {
   using T = __half;
+  static constexpr int kScale = 4096;   // 2^12: deviations of O(1e-4) keep 11 bits in FP16
   __device__ static __forceinline__ float ld(const T* p) { return __half2float(*p) * (1.0f / 4096.0f); }
   __device__ static __forceinline__ void st(T* p, float v) { *p = __float2half_rn(v * 4096.0f); }
+  __device__ static __forceinline__ float ld_raw(const T* p) { return __half2float(*p); }
+  __device__ static __forceinline__ void st_raw(T* p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Codec<ST_BF16> {
   using T = __nv_bfloat16;
+  static constexpr int kScale = 1;
   __device__ static __forceinline__ float ld(const T* p) { return __bfloat162float(*p); }
   __device__ static __forceinline__ void st(T* p, float v) { *p = __float2bfloat16_rn(v); }
+  __device__ static __forceinline__ float ld_raw(const T* p) { return __bfloat162float(*p); }
+  __device__ static __forceinline__ void st_raw(T* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 template <int ST> struct Compute { using R = float; };
 template <> struct Compute<ST_FP64> { using R = double; };
@@ -616,7 +631,10 @@ template <class R> __device__ __forceinline__ R relax_delta(R eps) {
   return fdiv((R)4 * eps, (R)1 + (R)2 * eps);
 }
 
-template <int Q, class R>
+// SCALE: g holds SCALE x h on entry and on return (the raw storage scale of the
+// interior path); the moments are taken back to h once, and the scale enters
+// the equilibrium weights and the force prefactor as constants.
+template <int Q, class R, int SCALE = 1>
 __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* u_out) {
   using L = Lat<Q>;
   R drho = 0, jx = 0, jy = 0, jz = 0;
@@ -626,6 +644,13 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
     if (L::c(i, 0)) jx += L::c(i, 0) > 0 ? g[i] : -g[i];
     if (L::c(i, 1)) jy += L::c(i, 1) > 0 ? g[i] : -g[i];
     if (L::c(i, 2)) jz += L::c(i, 2) > 0 ? g[i] : -g[i];
+  }
+  if (SCALE != 1) {
+    const R is = (R)1 / (R)SCALE;
+    drho *= is;
+    jx *= is;
+    jy *= is;
+    jz *= is;
   }
   // sum h c = rho u - U x - F/2: momentum relative to the reference velocity
   const R Fx = psel<R>(p.F[0], p.F_f[0]), Fy = psel<R>(p.F[1], p.F_f[1]), Fz = psel<R>(p.F[2], p.F_f[2]);
@@ -643,7 +668,7 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
   const R one_m_uu15 = (R)1 - (R)1.5 * (ux * ux + uy * uy + uz * uz);
   const R du15 = (R)1.5 * (dux * ((R)2 * U + dux) + uy * uy + uz * uz);
   // (1 - omega/2) w [3 (c - u).F + 9 (c.u)(c.F)] = (delta/2) [A_i (1 + 3 c.u) - 3 w u.F]
-  const R fpre = (R)0.5 * delta;
+  const R fpre = ((R)0.5 * (R)SCALE) * delta;
   const R uF3 = (R)3 * (ux * Fx + uy * Fy + uz * Fz);
   if (p.collision == 0) {
     // BGK over opposite pairs (i, i+1 = opp i): with s = c_i.u the equilibrium
@@ -653,7 +678,7 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
     //   F_{i / opp} = 3 s A_i - 3 w u.F  +/-  A_i      (A_i = 3 w c_i.F)
     const R wgt0 = (R)L::w(0);
     {
-      const R geq = wgt0 * (drho * one_m_uu15 - du15);
+      const R geq = (R)(L::w(0) * SCALE) * (drho * one_m_uu15 - du15);
       R gi = ((R)2 * geq - g[0]) + delta * (g[0] - geq);
       if (p.has_force) gi -= fpre * wgt0 * uF3;
       g[0] = gi;
@@ -666,8 +691,9 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
       const R su = cU + cdu;                                   // c_i . u
       const R eA = (R)4.5 * su * su + one_m_uu15;
       const R eD = (R)4.5 * cdu * (su + cU) - du15;
-      const R ev = w * (drho * eA + eD);
-      const R od = w * (R)3 * (drho * su + cdu);
+      const R wS = (R)(L::w(i) * SCALE);
+      const R ev = wS * (drho * eA + eD);
+      const R od = wS * (R)3 * (drho * su + cdu);
       const R gp = ev + od, gm = ev - od;                      // h^eq_i, h^eq_opp
       R np_ = ((R)2 * gp - g[i]) + delta * (g[i] - gp);
       R nm_ = ((R)2 * gm - g[i + 1]) + delta * (g[i + 1] - gm);
@@ -696,8 +722,9 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
     const R cdu = cdot<Q, R>(i, dux, uy, uz);
     const R cU = L::c(i, 0) > 0 ? U : (L::c(i, 0) < 0 ? -U : (R)0);
     const R su = cU + cdu;
-    const R ev = w * (drho * ((R)4.5 * su * su + one_m_uu15) + ((R)4.5 * cdu * (su + cU) - du15));
-    const R od = w * (R)3 * (drho * su + cdu);
+    const R wS = w * (R)SCALE;
+    const R ev = wS * (drho * ((R)4.5 * su * su + one_m_uu15) + ((R)4.5 * cdu * (su + cU) - du15));
+    const R od = wS * (R)3 * (drho * su + cdu);
     const R sp = (g[i] + g[i + 1]) - (R)2 * ev;
     const R dp = (g[i] - g[i + 1]) - (R)2 * od;
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
@@ -716,7 +743,7 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
   const R tr = (pxx + pyy + pzz) * ((R)1 / (R)3);
   {
     const R wgt0 = (R)L::w(0);
-    R gi = wgt0 * (drho * one_m_uu15 - du15) + dm1 * (wgt0 * (R)4.5 * -tr);
+    R gi = (wgt0 * (R)SCALE) * (drho * one_m_uu15 - du15) + dm1 * (wgt0 * (R)4.5 * -tr);
     if (p.has_force) gi -= fpre * wgt0 * uF3;
     g[0] = gi;
   }

@@ -42,7 +42,8 @@ __device__ __forceinline__ NbOff nb_offsets(const Params& p, int x, int y, int z
 }
 
 // Everything after streaming for a cell with in-lattice (or periodic)
-// neighbours: SA update, relaxation rate, collision, stores.
+// neighbours: SA update, relaxation rate, collision, stores.  g holds the
+// pulled populations in the raw storage scale (Codec::ld_raw).
 template <int Q, int ST>
 __device__ __forceinline__ void interior_finish(const Params& p, const NbOff& o,
                                                 typename Compute<ST>::R (&g)[Q], int x, int y) {
@@ -64,10 +65,10 @@ __device__ __forceinline__ void interior_finish(const Params& p, const NbOff& o,
   const R delta = relax_delta<R>((R)3 * (nu + nut));   // 2 - omega (Eq. 8)
   // moments and collision
   R u[3];
-  collide<Q, R>(p, g, delta, u);
+  collide<Q, R, C::kScale>(p, g, delta, u);   // g in raw storage scale
   // store
 #pragma unroll
-  for (int i = 0; i < Q; ++i) C::st(fd + (i * o.nc + o.id), g[i]);
+  for (int i = 0; i < Q; ++i) C::st_raw(fd + (i * o.nc + o.id), g[i]);
   st_rec(vd, o.id, u[0], u[1], u[2], ntn);
 }
 
@@ -87,7 +88,7 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
     const int off = (cx > 0 ? o.oxm : (cx < 0 ? o.oxp : 0)) + (cy > 0 ? o.oym : (cy < 0 ? o.oyp : 0)) +
                     (cz > 0 ? o.ozm : (cz < 0 ? o.ozp : 0));
-    g[i] = (R)C::ld(fs + (i * o.nc + o.id + off));
+    g[i] = (R)C::ld_raw(fs + (i * o.nc + o.id + off));
   }
   interior_finish<Q, ST>(p, o, g, x, y);
 }
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(256, LBM_TMA_MINB)
     if (active && (p.px || (x != 0 && x != p.nx - 1))) {
       R g[Q];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) g[i] = (R)C::ld(st + (i * BH + ty) * BW + tx + XOFF - L::c(i, 0));
+      for (int i = 0; i < Q; ++i) g[i] = (R)C::ld_raw(st + (i * BH + ty) * BW + tx + XOFF - L::c(i, 0));
       const NbOff o = nb_offsets(p, x, y, z);
       interior_finish<Q, ST>(p, o, g, x, y);
     }
