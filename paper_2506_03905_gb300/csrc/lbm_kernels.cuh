@@ -646,19 +646,23 @@ __global__ void k_fields(const Params p, double* rho, double* u, double* nut, do
       r += gi;
     }
     if (rho) rho[k] = r * rho0;
-    const Rec<R> rec = ld_rec(vs, id);
+    double ntl, ux0 = 0.0;
     if (u) {
-      u[k] = (double)rec.x * vel;
+      const Rec<R> rec = ld_rec(vs, id);
+      ux0 = (double)rec.x;
+      u[k] = ux0 * vel;
       u[k + n] = (double)rec.y * vel;
       u[k + 2 * n] = (double)rec.z * vel;
+      ntl = (double)rec.n;
+    } else {
+      ntl = (double)vs[4 * id + 3];   // nu_tilde alone
     }
-    const double ntl = (double)rec.n;
     if (nt) nt[k] = ntl * visc;
     if (nut) {
       const double chi = ntl / p.nu, c3 = chi * chi * chi;
       nut[k] = p.turbulent ? ntl * c3 / (c3 + 7.1 * 7.1 * 7.1) * visc : 0.0;
     }
-    fin = fin && isfinite((double)rec.x) && isfinite(ntl);
+    fin = fin && isfinite(ux0) && isfinite(ntl);
     if (!fin) atomicOr(p.flags, FLAG_NONFINITE);
   }
 }
