@@ -459,6 +459,8 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
   build_tensor_maps(c);
   // float copies of the lattice parameters for the FP32 kernels
   p.nu_f = (float)p.nu;
+  p.inv_nu = 1.0 / p.nu;
+  p.inv_nu_f = (float)p.inv_nu;
   p.Ush_f = (float)p.Ush;
   for (int a = 0; a < 3; ++a) p.F_f[a] = (float)p.F[a];
   for (int i = 0; i < 19; ++i) p.guoA_f[i] = (float)p.guoA[i];

@@ -144,12 +144,13 @@ struct Params {
   int wall_law;                // 0 Eq. 16, 1 log law
   int has_force;
   double nu;                   // molecular viscosity (lattice)
+  double inv_nu;               // 1 / nu
   double F[3];                 // body force density (lattice)
   double guoA[19];             // 3 w_i c_i.F per direction (Guo forcing coefficient)
   double Ush;                  // reference velocity U (x) of the stored deviations
   // float copies for the FP32 kernels: converting a double per thread would run
   // on the FP64 pipe, which on GB300 has 1/64 of the FP32 rate
-  float nu_f, F_f[3], guoA_f[19], Ush_f, xs_lb_f[2], u_face_f[4][3], nt_face_f[4], d_w_f[2],
+  float nu_f, inv_nu_f, F_f[3], guoA_f[19], Ush_f, xs_lb_f[2], u_face_f[4][3], nt_face_f[4], d_w_f[2],
       ibb_f[2][4];
   double law_kappa, law_B;
   int kind[6];                 // face kinds
@@ -234,18 +235,18 @@ template <class R> __device__ __forceinline__ R sa_fv1(R chi) {
   return c3 / (c3 + cv * cv * cv);
 }
 
-// nu_t = nu_tilde f_v1(nu_tilde / nu) (Eq. 10)
-template <class R> __device__ __forceinline__ R sa_nut(R nt, R nu) {
-  const R chi = fdiv(nt, nu);
+// nu_t = nu_tilde f_v1(nu_tilde / nu) (Eq. 10); inv_nu = 1 / nu
+template <class R> __device__ __forceinline__ R sa_nut(R nt, R inv_nu) {
+  const R chi = nt * inv_nu;
   const R c3 = chi * chi * chi;
   return nt * fdiv(c3, c3 + (R)(SAConst::cv1 * SAConst::cv1 * SAConst::cv1));
 }
 
 // P - D of Eq. 12 with S~ (Eq. 13, kept positive by the ICCFD7 limiter) and r, f_w (Eq. 14)
-template <class R> __device__ __forceinline__ R sa_source(R nt, R S, R nu, R inv_d2) {
+template <class R> __device__ __forceinline__ R sa_source(R nt, R S, R inv_nu, R inv_d2) {
   const R kap = (R)SAConst::kappa;
   const R cw1 = (R)SAConst::cb1 / (kap * kap) + ((R)1 + (R)SAConst::cb2) / (R)SAConst::sigma;
-  const R chi = fdiv(nt, nu);
+  const R chi = nt * inv_nu;
   const R c3 = chi * chi * chi;
   const R fv1 = fdiv(c3, c3 + (R)(SAConst::cv1 * SAConst::cv1 * SAConst::cv1));
   const R fv2 = (R)1 - fdiv(chi, (R)1 + chi * fv1);
@@ -374,7 +375,7 @@ __device__ R sa_update(const Params& p, const R* __restrict__ v, int x, int y, i
     grad2 += g * g;
   }
   const R inv_d2 = inv_wall_dist2<R>(p, x, y);
-  const R rhs = -conv + sa_source<R>(c.nt, S, nu, inv_d2) +
+  const R rhs = -conv + sa_source<R>(c.nt, S, psel<R>(p.inv_nu, p.inv_nu_f), inv_d2) +
                 (diff + (R)SAConst::cb2 * grad2) * (R)(1.0 / SAConst::sigma);
   const R nn = c.nt + rhs;
   return nn > (R)0 ? nn : (R)0;
@@ -425,7 +426,7 @@ __device__ __forceinline__ R sa_update_interior(const Params& p, const R* __rest
     grad2 += g * g;
   }
   const R inv_d2 = inv_wall_dist2<R>(p, x, y);
-  const R rhs = -conv + sa_source<R>(c, S, nu, inv_d2) +
+  const R rhs = -conv + sa_source<R>(c, S, psel<R>(p.inv_nu, p.inv_nu_f), inv_d2) +
                 (diff + (R)SAConst::cb2 * grad2) * (R)(1.0 / SAConst::sigma);
   const R nn = c + rhs;
   return nn > (R)0 ? nn : (R)0;
@@ -637,13 +638,16 @@ template <class R> __device__ __forceinline__ R relax_delta(R eps) {
 template <int Q, class R, int SCALE = 1>
 __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* u_out) {
   using L = Lat<Q>;
-  R drho = 0, jx = 0, jy = 0, jz = 0;
+  // moments over opposite pairs (i, i+1 = opp i): the pair's sum enters rho,
+  // its difference rho u
+  R drho = g[0], jx = 0, jy = 0, jz = 0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    drho += g[i];
-    if (L::c(i, 0)) jx += L::c(i, 0) > 0 ? g[i] : -g[i];
-    if (L::c(i, 1)) jy += L::c(i, 1) > 0 ? g[i] : -g[i];
-    if (L::c(i, 2)) jz += L::c(i, 2) > 0 ? g[i] : -g[i];
+  for (int i = 1; i < Q; i += 2) {
+    const R sp = g[i] + g[i + 1], dp = g[i] - g[i + 1];
+    drho += sp;
+    if (L::c(i, 0)) jx += L::c(i, 0) > 0 ? dp : -dp;
+    if (L::c(i, 1)) jy += L::c(i, 1) > 0 ? dp : -dp;
+    if (L::c(i, 2)) jz += L::c(i, 2) > 0 ? dp : -dp;
   }
   if (SCALE != 1) {
     const R is = (R)1 / (R)SCALE;

@@ -61,7 +61,7 @@ __device__ __forceinline__ void interior_finish(const Params& p, const NbOff& o,
   else
     ntn = vs[4 * o.id + 3];
   const R nu = psel<R>(p.nu, p.nu_f);
-  const R nut = p.turbulent ? sa_nut<R>(ntn, nu) : (R)0;
+  const R nut = p.turbulent ? sa_nut<R>(ntn, psel<R>(p.inv_nu, p.inv_nu_f)) : (R)0;
   const R delta = relax_delta<R>((R)3 * (nu + nut));   // 2 - omega (Eq. 8)
   // moments and collision
   R u[3];
@@ -163,7 +163,7 @@ __device__ __forceinline__ void bulk_wall_bb(const Params& p, int fi, int x, int
   // the Dirichlet nu_tilde_B the wall pass wrote into this step's record
   const R ntB = vd[4 * o.id + 3];
   const R nu = psel<R>(p.nu, p.nu_f);
-  const R nut = p.turbulent ? sa_nut<R>(ntB, nu) : (R)0;
+  const R nut = p.turbulent ? sa_nut<R>(ntB, psel<R>(p.inv_nu, p.inv_nu_f)) : (R)0;
   const R delta = relax_delta<R>((R)3 * (nu + nut));
   R u[3];
   collide<Q, R>(p, g, delta, u);
@@ -214,7 +214,7 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
     ntn = vs[4 * id + 3];
   }
   const R nu = psel<R>(p.nu, p.nu_f);
-  const R nut = p.turbulent ? sa_nut<R>(ntn, nu) : (R)0;
+  const R nut = p.turbulent ? sa_nut<R>(ntn, psel<R>(p.inv_nu, p.inv_nu_f)) : (R)0;
   const R delta = relax_delta<R>((R)3 * (nu + nut));   // 2 - omega (Eq. 8)
 
   // 2. post-stream populations
@@ -555,7 +555,7 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
       G[1][c] = (R)s * dn;
     }
     const R ntB = vs[4 * idB + 3];
-    const R nutB = p.turbulent ? sa_nut<R>(ntB, (R)nu) : (R)0;
+    const R nutB = p.turbulent ? sa_nut<R>(ntB, psel<R>(p.inv_nu, p.inv_nu_f)) : (R)0;
     const R tau = (R)0.5 + (R)3 * ((R)nu + nutB);
     const R Sxx = G[0][0], Syy = G[1][1], Szz = G[2][2];
     const R Sxy = (R)0.5 * (G[0][1] + G[1][0]), Sxz = (R)0.5 * (G[0][2] + G[2][0]),
