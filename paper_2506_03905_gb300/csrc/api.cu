@@ -536,7 +536,7 @@ void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b) {
   int bx = 32;
   while (bx > 1 && bx / 2 >= c->nx) bx /= 2;
   const int nrows = rows == ROWS_ALL ? c->ny : (rows == ROWS_WALL ? 2 : c->ny - 2);
-  int by = 256 / bx;
+  int by = LBM_BULK_THREADS / bx;
   if (rows == ROWS_WALL) by = 2;
   if (rows == ROWS_XEDGE) {
     *b = dim3(2, 64, 1);

@@ -100,16 +100,19 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
 // GENERAL = false: the launch holds only cells without a non-periodic face
 // within one cell (checked by the host), so the face logic is not compiled in.
 // Minimum resident blocks per SM requested from the compiler for k_bulk
-// (sets its register budget; 0 leaves the choice to the compiler).  Four
-// blocks of 256 threads (<= 64 registers) measured fastest on GB300 for the
-// D3Q19 FP32 channel: 0.159 ms against 0.172 ms with the compiler's 80.
+// (sets its register budget; 0 leaves the choice to the compiler).  A budget
+// of 64 registers (1024 threads per SM) measured fastest on GB300 for the
+// D3Q19 FP32 channel (0.159 ms per step against 0.172 ms with the
+// compiler's 80), and blocks of 128 threads faster than 256 or 512 (0.137 /
+// 0.143 / 0.153 ms per step: the wall pass and the wall rows interleave
+// better with the inner rows' smaller blocks).
 #ifndef LBM_BULK_MINB
-#define LBM_BULK_MINB 4
+#define LBM_BULK_MINB 8
 #endif
 #if LBM_BULK_MINB > 0
-#define LBM_BULK_BOUNDS __launch_bounds__(256, LBM_BULK_MINB)
+#define LBM_BULK_BOUNDS __launch_bounds__(LBM_BULK_THREADS, LBM_BULK_MINB)
 #else
-#define LBM_BULK_BOUNDS __launch_bounds__(256)
+#define LBM_BULK_BOUNDS __launch_bounds__(LBM_BULK_THREADS)
 #endif
 
 // A bounce-back wall node on a lattice with periodic x: the sources of the
