@@ -538,9 +538,10 @@ void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b) {
   const int nrows = rows == ROWS_ALL ? c->ny : (rows == ROWS_WALL ? 2 : c->ny - 2);
   int by = LBM_BULK_THREADS / bx;
   if (rows == ROWS_WALL) by = 2;
-  if (rows == ROWS_XEDGE) {
-    *b = dim3(2, 64, 1);
-    *g = dim3(1, (nrows + 63) / 64, c->nz);
+  if (rows == ROWS_XEDGE) {   // columns 0 and nx-1: 2 x (LBM_BULK_THREADS / 2) cells per block
+    const int h = LBM_BULK_THREADS / 2;
+    *b = dim3(2, h, 1);
+    *g = dim3(1, (nrows + h - 1) / h, c->nz);
     return;
   }
   *b = dim3(bx, by, 1);
