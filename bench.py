@@ -3,15 +3,20 @@
 
 Workload (N = 1): the 3-D D3Q19 turbulent channel in FP32 storage,
 256 x 128 x 128 cells, periodic in x and z, slip-velocity bounce-back walls
-(Eq. 35) on both y faces, Re_tau = 5200, SA turbulence model, initial
-u_x = U_b (1 +/- 1 %) seeded.  A step is one full pass of the method: the
-wall pre-pass kernel and the fused SA + stream + collide kernel.  The
-population buffers (2 x 319 MB) are larger than the 129 MB L2, so no flush is
-needed between steps.
+(Eq. 35, with Yu's rule of Eq. 37 at d_w = 1/2) on both y faces,
+Re_tau = 5200, SA turbulence model, initial u_x = U_b (1 +/- 1 %) seeded and
+nu_tilde = max(3 nu, kappa u_tau d).  A step is one full pass of the method:
+the wall pre-pass, the wall rows and the fused SA + stream + collide kernel
+on the inner rows (three launches).  The population buffers (2 x 319 MB) are
+larger than the 129 MB L2, so no flush is needed between steps.
 
-Extra keys report the HRFD wall scheme, FP16/BF16 shifted storage and the
-batched mesh-sensitivity sweep on the same GPU.  ``--impl reference`` times the
-FP64 CPU oracle on a bounded crop of the same workload.
+Extra keys report the HRFD and Cai-Degrigny walls, FP16/BF16 shifted
+storage, the 2048 x 512 x 8 flat plate and the 96-instance batched sweep on
+the same GPU.  ``--impl reference`` times the FP64 CPU oracle, one
+single-threaded copy per host core, on bounded crops of the same workload;
+``cpu_baseline`` in the main line is the same on 64 x 128 x 8 crops plus one
+copy alone.  ``--profile-case`` and ``--profile-batch`` are short runs for
+ncu.
 
 Multi-GPU: one process per GPU (torchrun); every rank advances its own
 replica of the workload (weak scaling, no data-path collective); the timed
