@@ -33,9 +33,9 @@ enum { FLAG_NONFINITE = 1u, FLAG_NEWTON = 2u, FLAG_TMA_TIMEOUT = 4u };
 // columns 0 and nx-1 of rows 1..ny-2 (the x-face cells of a non-periodic x
 // axis, which both inner-row kernels leave out).
 enum { ROWS_ALL = 0, ROWS_INNER = 1, ROWS_WALL = 2, ROWS_XEDGE = 3 };
-// threads per k_bulk block (x fastest: 32 x 4 cells for nx >= 32)
+// threads per k_bulk block (x fastest: 32 x 2 cells for nx >= 32)
 #ifndef LBM_BULK_THREADS
-#define LBM_BULK_THREADS 128
+#define LBM_BULK_THREADS 64
 #endif
 constexpr int RED_THREADS = 256;   // FP64 reduction block size
 constexpr int RED_VALS = 4;        // mass, momentum x/y/z

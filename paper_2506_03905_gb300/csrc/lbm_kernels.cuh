@@ -103,11 +103,11 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
 // (sets its register budget; 0 leaves the choice to the compiler).  A budget
 // of 64 registers (1024 threads per SM) measured fastest on GB300 for the
 // D3Q19 FP32 channel (0.159 ms per step against 0.172 ms with the
-// compiler's 80), and blocks of 128 threads faster than 256 or 512 (0.137 /
-// 0.143 / 0.153 ms per step: the wall pass and the wall rows interleave
-// better with the inner rows' smaller blocks).
+// compiler's 80), and small blocks faster than large ones: 64 / 128 / 256 /
+// 512 threads gave 0.135 / 0.137 / 0.143 / 0.153 ms per step (the wall pass
+// and the wall rows interleave better with the inner rows' smaller blocks).
 #ifndef LBM_BULK_MINB
-#define LBM_BULK_MINB 8
+#define LBM_BULK_MINB 16
 #endif
 #if LBM_BULK_MINB > 0
 #define LBM_BULK_BOUNDS __launch_bounds__(LBM_BULK_THREADS, LBM_BULK_MINB)
