@@ -1,5 +1,5 @@
-"""The seeded workload definitions (lbm_cases): the recipes the design doc states
-for the initial fields and the wall rules, checked on small instances."""
+"""The seeded workload definitions (lbm_cases): the stated recipes for the
+initial fields and the wall rules, checked on small instances."""
 import numpy as np
 
 import lbm_cases as C

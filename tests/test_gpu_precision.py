@@ -65,10 +65,11 @@ def test_plate_storage_precision(scheme):
         got = s.fields(names)
         s.close()
         report[storage] = _errors(case, got, ref, x)
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    os.makedirs(out, exist_ok=True)
-    with open(os.path.join(out, f"precision_plate_{scheme}.json"), "w") as fh:
-        json.dump(dict(case=base.name, steps=NSTEPS, errors=report), fh, indent=1)
+    out = os.environ.get("LBM_REPORT_DIR")   # optional: keep the error report as JSON
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, f"precision_plate_{scheme}.json"), "w") as fh:
+            json.dump(dict(case=base.name, steps=NSTEPS, errors=report), fh, indent=1)
     assert report["fp32"]["cf_max_rel"] < 1e-5, report
     for st in ("fp16", "bf16"):
         assert report[st]["cf_max_rel"] < 1e-2, (st, report)
