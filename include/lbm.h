@@ -252,8 +252,9 @@ lbm_status lbm_moments_noalloc(const void* f, int lattice, int storage, int nx, 
 /* ------------------------------------------------------------------------
  * Batched sweeps: many independent contexts advanced together by one
  * persistent, cooperative kernel launch per lbm_batch_step call (captured in
- * a CUDA graph).  Work items are (instance, tile) pairs; a bounded grid
- * barrier separates the wall pre-pass and bulk phases of every step.
+ * a CUDA graph).  Work items, each taken by one warp, are chunks of 32 wall
+ * nodes or ranges of cells of one instance; a bounded grid barrier separates
+ * the wall pre-pass and bulk phases of every step.
  * Instances keep their own configurations and boundary conditions; the
  * contexts must have been created and initialised (lbm_set_fields) first and
  * must share one stream.  The batch does not own the contexts.
