@@ -55,17 +55,25 @@ def nu_t(nt, nu):
     return nt * fv1(nt / nu)
 
 
+def s_tilde(nt, S, nu, inv_d2):
+    """Modified vorticity of Eq. 13, S~ = S + Sbar with Sbar = nu_tilde f_v2 / (kappa d)^2,
+    kept positive by the ICCFD7 limiter: where Sbar < -c_v2 S the value is
+    S + S (c_v2^2 S + c_v3 Sbar) / ((c_v3 - 2 c_v2) S - Sbar), which meets S + Sbar at
+    Sbar = -c_v2 S and tends to (1 - c_v3) S as Sbar -> -inf."""
+    chi = nt / nu
+    sbar = nt * fv2(chi) * (inv_d2 / KAPPA ** 2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        lim = S + S * (CV2_LIM ** 2 * S + CV3_LIM * sbar) / ((CV3_LIM - 2.0 * CV2_LIM) * S - sbar)
+    return np.where(sbar >= -CV2_LIM * S, S + sbar, lim)
+
+
 def source(nt, S, nu, inv_d2):
     """P - D of Eq. 12 with S~ of Eq. 13 and r of Eq. 14.
 
     ``S`` is the vorticity magnitude, ``inv_d2`` = 1 / d^2 (0 with no wall).
     """
-    chi = nt / nu
     inv_kd2 = inv_d2 / KAPPA ** 2
-    sbar = nt * fv2(chi) * inv_kd2
-    with np.errstate(divide="ignore", invalid="ignore"):
-        lim = S + S * (CV2_LIM ** 2 * S + CV3_LIM * sbar) / ((CV3_LIM - 2.0 * CV2_LIM) * S - sbar)
-    st = np.where(sbar >= -CV2_LIM * S, S + sbar, lim)
+    st = s_tilde(nt, S, nu, inv_d2)
     with np.errstate(divide="ignore", invalid="ignore"):
         r = np.where(st > 0.0, np.minimum(nt * inv_kd2 / st, RLIM), RLIM)
     P = CB1 * st * nt

@@ -344,7 +344,12 @@ class Oracle:
 
     def hrfd(self, f, nt_new):
         """Stage 6: regularized wall nodes with the HRFD gradient (Section 3.1),
-        or with the Cai-Degrigny gradient (Section 3.1.2, Eq. 29)."""
+        or with the Cai-Degrigny gradient (Section 3.1.2, Eq. 29).
+
+        Parity pinned: the rebuilt populations carry rho_B (Eq. 23), rho_B u_B and
+        the non-equilibrium second moment -2 rho_B tau_eff c_s^2 S with S written
+        out from Eqs. 15, 27-28 (and Eq. 29) on states whose finite differences are
+        known in closed form, for beta in {0, 0.28, 1}."""
         vs = self.vs
         Q = L.second_order_Q(vs)
         _, up = self._pad(self.nt, self.u)

@@ -99,3 +99,45 @@ def test_vorticity_of_rigid_rotation():
     r = sa.rhs(_pad_linear(nt), _pad_linear(u), nu, inv_d2)
     # P = c_b1 * S~ * nt with S~ = S = 2 Omega; D = 0; no diffusion; convection 0
     assert np.allclose(r, sa.CB1 * 2 * Om * 1e-3, rtol=1e-12)
+
+
+def _sbar_state(sbar_over_S, S=2e-3, nu=1e-4):
+    """(nt, S, nu, inv_d2) with Sbar = nt f_v2 / (kappa d)^2 equal to sbar_over_S * S:
+    chi = 10 makes f_v2 negative, and 1/d^2 is solved for."""
+    nt = 10.0 * nu
+    fv2 = sa.fv2(np.array(10.0))
+    assert fv2 < 0
+    inv_d2 = sbar_over_S * S * sa.KAPPA ** 2 / (nt * fv2)
+    return nt, S, nu, inv_d2
+
+
+def test_s_tilde_limiter_second_branch():
+    """Eq. 13 with the ICCFD7 limiter (c_v2 = 0.7, c_v3 = 0.9) where Sbar < -c_v2 S:
+    the branch meets S + Sbar = (1 - c_v2) S = 0.3 S at the switch, equals
+    S (1 + (c_v2^2 - c_v3) / (c_v3 - 2 c_v2 + 1)) = 0.18 S at Sbar = -S, tends to
+    (1 - c_v3) S = 0.1 S as Sbar -> -inf and stays positive and increasing."""
+    S = 2e-3
+    st = lambda k: float(sa.s_tilde(*_sbar_state(k, S)))  # noqa: E731
+    assert st(-0.7) == pytest.approx(0.3 * S, rel=1e-12)
+    assert st(-0.7 - 1e-9) == pytest.approx(0.3 * S, rel=1e-7)
+    assert st(-0.7 + 1e-9) == pytest.approx(0.3 * S, rel=1e-7)
+    assert st(-1.0) == pytest.approx(0.18 * S, rel=1e-12)
+    assert st(-1e8) == pytest.approx(0.1 * S, rel=1e-6)
+    ks = -np.logspace(np.log10(0.7), 6, 200)
+    vals = np.array([st(k) for k in ks])
+    assert np.all(vals > 0.1 * S) and np.all(np.diff(vals) < 0)
+    # the first branch, S + Sbar, is untouched above the switch
+    assert st(-0.5) == pytest.approx(0.5 * S, rel=1e-12)
+    assert st(2.0) == pytest.approx(3.0 * S, rel=1e-12)
+
+
+def test_source_uses_the_limited_s_tilde():
+    """P of Eq. 12 is c_b1 S~ nu_tilde on the limited branch, and r of Eq. 14 is
+    taken with the limited S~: at Sbar = -S (S~ = 0.18 S) the source equals
+    c_b1 0.18 S nt - c_w1 f_w(r) nt^2 / d^2 with r = min(nt / (0.18 S kappa^2 d^2), 10)."""
+    S = 2e-3
+    nt, S, nu, inv_d2 = _sbar_state(-1.0, S)
+    r = min(nt * inv_d2 / (sa.KAPPA ** 2 * 0.18 * S), sa.RLIM)
+    ref = sa.CB1 * 0.18 * S * nt - sa.CW1 * float(sa.fw(np.array(r))) * nt * nt * inv_d2
+    assert float(sa.source(np.array(nt), np.array(S), nu, np.array(inv_d2))) == \
+        pytest.approx(ref, rel=1e-12)

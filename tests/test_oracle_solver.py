@@ -294,3 +294,27 @@ def test_cai_degrigny_wall_runs_and_is_beta_one_limit():
     o.run(20)
     assert np.isfinite(o.fs).all()
     assert np.all(o.utau["ymin"] > 0)
+
+
+def test_freestream_face_imposes_equilibrium():
+    """Free-stream face: every population entering through it is f^eq(rho0, U_inf),
+    whatever the state inside.  (i) The uniform free stream is a fixed point of a
+    step with that face; (ii) after a perturbed interior is streamed, the entering
+    populations of the top row equal those a uniform U_inf state carries."""
+    c = C.flat_plate_3d(nx=12, ny=8, nz=2, dx=4e-2, scheme="wall_bb").replace(
+        bcs={"ymin": C.BC("symmetry"), "xmin": C.BC("periodic"), "xmax": C.BC("periodic")},
+        turbulence="laminar")
+    o = make(c)
+    f0 = o.fs.copy()
+    o.run(3)
+    assert np.abs(o.fs - f0).max() < 1e-15               # (i)
+    rho, u, nut = C.initial_fields(c)
+    rng = np.random.default_rng(7)
+    u = u * (1.0 + 0.05 * rng.uniform(-1, 1, size=u.shape))
+    rho = rho * (1.0 + 0.01 * rng.uniform(-1, 1, size=rho.shape))
+    o2 = Oracle(c, rho, u, nut)
+    f = o2.y_faces(o2.stream(), {})
+    top = o2.vs.c[:, 1] < 0                               # entering through ymax
+    assert np.abs(f[top][:, :, -1, :] - f0[top][:, :, -1, :]).max() < 1e-16     # (ii)
+    # the face is not a copy of the interior: the perturbed interior differs
+    assert np.abs(f[top][:, :, -2, :] - f0[top][:, :, -2, :]).max() > 1e-4
