@@ -348,7 +348,9 @@ def batched_variant(pkg, torch, steps, rank=0, world=1, storage="fp32"):
         solvers.append(s)
     total = sum(c.cells for c in cases)
     out = {}
-    # per-case sequential runs (each graph-replayed)
+    # per-case sequential runs through lbm_step: every instance of the sweep is
+    # below the size at which steps of lattices with walls are launched directly,
+    # so each replays its captured two-step graphs
     for s in solvers:
         s.step(steps)
     torch.cuda.synchronize()
@@ -369,8 +371,17 @@ def batched_variant(pkg, torch, steps, rank=0, world=1, storage="fp32"):
         pkg.lbm_batch_step(b, steps)
         torch.cuda.synchronize()
         bt = time.perf_counter() - t0
+        info = pkg.lbm_batch_info(b)
+        st = pkg.lbm_batch_wait(b)
+        alg = sum(ALG_BYTES[(c.lattice, c.storage)] * c.cells for c in cases)
+        peak, _ = measured_peaks()
         out[f"batched_{storage}"] = {"mlups": round(total * steps / bt / 1e6, 1),
-                                     "instances": len(cases), "cells": total}
+                                     "instances": len(cases), "cells": total,
+                                     "alg_bytes_per_cell": round(alg / total, 1),
+                                     "frac_of_hbm": round(alg * steps / bt / 1e9 / peak, 4),
+                                     "use_graph": info["use_graph"], "threads": info["threads"],
+                                     "tile": info["tile"], "items_per_step": info["items_per_step"],
+                                     "status": int(st)}
     finally:
         pkg.lbm_batch_destroy(b)
         for s in solvers:

@@ -142,14 +142,23 @@ typedef struct {
   double max_rel_du_tau;       /* max |u_tau - u_tau_prev| / u_tau over wall nodes since
                                   the previous lbm_diagnostics call (Section 4.1.1 criterion) */
   int nonfinite;               /* 1 if any population was NaN/Inf */
-  int newton_failures;         /* wall nodes where the Newton iteration hit its limit */
+  int newton_failures;         /* wall-node updates whose Newton iteration reached its
+                                  100-iteration limit since the state was set (a count
+                                  summed over steps and nodes; the last iterate is used) */
 } lbm_diag;
 
 typedef struct lbm_ctx lbm_ctx;
 
-/* Create a solver for one lattice; all faces start periodic.  Validates the
-   configuration (tau > 1/2, sizes, enum values).  On success *out owns all
-   device state; on failure *out is NULL. */
+/* Create a solver for one lattice (Section 2.1: the D2Q9 / D3Q19 velocity sets
+   of Eq. 3; Eq. 8 for the relaxation time; the acoustic scaling of Section
+   4.1.1, dt = M dx / (sqrt(3) U_ref), converts cfg's SI inputs to lattice units).
+   All faces start periodic.  Validates the configuration: tau0 = 1/2 + 3 nu_lb
+   must exceed 1/2, sizes positive (nz = 1 for D2Q9), Q x padded cells < 2^31,
+   enum values known; returns LBM_EINVAL (or LBM_EUNSUPPORTED for a lattice too
+   large for 32-bit indexing) with the reason in lbm_last_error(NULL).
+   cfg is copied; the caller keeps ownership of it.  On success *out owns all
+   device state (allocated through cfg->alloc if set, else cudaMalloc); on
+   failure *out is NULL and nothing is leaked (LBM_ENOMEM, LBM_ECUDA). */
 lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out);
 
 /* Set the condition of one face (LBM_XMIN..LBM_ZMAX) before the first
@@ -164,9 +173,20 @@ lbm_status lbm_set_bc(lbm_ctx* ctx, int face, const lbm_bc* bc);
 lbm_status lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* u,
                           const double* nu_tilde, int on_device);
 
-/* Enqueue nsteps full steps (SA update, wall pre-pass, stream, face
-   conditions, HRFD wall reconstruction, moments, collision) on cfg.stream.
-   Steps are replayed from a captured CUDA graph. */
+/* Enqueue nsteps full steps on cfg.stream, each in the order SA update
+   (Section 2.2, Eqs. 10-14, explicit Euler), bounce-back wall pre-pass (Section
+   3.2, Eqs. 31-35 with the Newton inversion of Eq. 16 or the log law), pull
+   streaming (Eq. 3) with the face conditions, regularized wall reconstruction
+   (Section 3.1, Eqs. 19-28, or Eq. 29), moments (Eqs. 4-5) and collision with
+   omega from nu + nu_t (Eq. 8).  Returns once the work is enqueued (no host
+   synchronisation).  A lattice with walls and at least 2^21 cells launches each
+   step's three kernels directly, so that the wall pre-pass overlaps the inner
+   rows on a high-priority stream; other lattices replay pairs of steps from
+   captured CUDA graphs (one per buffer parity).  Errors: LBM_EINVAL for nsteps < 0 or
+   no state yet (lbm_set_fields / lbm_set_state first), face validation errors
+   of the first step, LBM_ECUDA for a failed launch or capture.  Device-side
+   failures (non-finite values, Newton limit) are reported by the next call
+   that synchronises (lbm_fields, lbm_diagnostics). */
 lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
 
 /* Same steps launched without a graph, with CUDA events around every kernel;
@@ -175,13 +195,26 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
 lbm_status lbm_step_timed(lbm_ctx* ctx, int nsteps, float kernel_ms[2]);
 
 /* Copy the fields selected by mask (LBM_FIELD_*) into caller buffers dst[k]
-   (float64, physical units), in increasing bit order.  dst_on_device != 0:
-   device pointers, else host pointers.  Synchronises cfg.stream and returns
-   LBM_ENONFINITE if the state holds NaN/Inf. */
+   (float64, physical units), in increasing bit order: rho = sum f_i (Eq. 4) and
+   u (Eq. 5, with the F/2 shift) of the last collision, nu_t = nu_tilde f_v1
+   (Eq. 10), nu_tilde, and per wall node u_tau (Newton on Eq. 16 / the log law)
+   and C_f = 2 (u_tau / U_ref)^2 (the skin-friction coefficient of Section 4.2.2
+   with U_ref the reference speed of cfg).  dst_on_device != 0: device pointers,
+   else host pointers; the caller owns them and sizes them as the LBM_FIELD_*
+   comments state.  Synchronises cfg.stream.  Returns LBM_ENONFINITE if the
+   state holds NaN/Inf and LBM_ENEWTON if the u_tau inversion reached its
+   iteration limit at some wall node since the state was set (the fields are
+   copied in both cases); LBM_EINVAL for unknown mask bits, a NULL dst entry or
+   no state yet. */
 lbm_status lbm_fields(lbm_ctx* ctx, unsigned mask, void* const* dst, int dst_on_device);
 
 /* FP64 reductions over the lattice (deterministic order) into *out, host
-   memory.  Synchronises cfg.stream. */
+   memory: total mass and momentum of the post-collision populations (the
+   quantities Eq. 23 of Section 3.1 is built to conserve), mean u_tau per wall
+   and the relative u_tau change of the convergence criterion (Section 4.1.1).
+   Synchronises cfg.stream.  Non-finite values and Newton failures are reported
+   in *out (nonfinite, newton_failures) with LBM_OK; LBM_ETIMEOUT if a bounded
+   device-side wait gave up. */
 lbm_status lbm_diagnostics(lbm_ctx* ctx, lbm_diag* out);
 
 /* Convergence-driven run (Section 4.1.1: runs are converged when the relative
@@ -211,7 +244,10 @@ size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_get_state(lbm_ctx* ctx, void* dst);
 lbm_status lbm_set_state(lbm_ctx* ctx, const void* src);
 
-/* Release everything the context owns; NULL is allowed. */
+/* Release everything the context owns (after synchronising its stream):
+   device buffers through cfg.free (or cudaFree), captured graphs, the side
+   streams and events.  Caller memory is never freed.  NULL is allowed.  A batch
+   that holds the context must be destroyed first. */
 void lbm_destroy(lbm_ctx* ctx);
 
 /* Message of the last failure of this context (static storage if ctx is NULL). */
@@ -223,6 +259,21 @@ const char* lbm_last_error(const lbm_ctx* ctx);
    count that never synchronises; 0 for NULL.  Bookkeeping for benchmarks: the
    paper has no counterpart. */
 unsigned long long lbm_kernel_launches(const lbm_ctx* ctx);
+
+/* Steps advanced since lbm_create (lbm_step, lbm_step_timed, lbm_run_to_convergence
+   and batch launches that include the context); -1 for NULL.  Bookkeeping: the
+   paper has no counterpart. */
+long long lbm_steps_done(const lbm_ctx* ctx);
+
+/* Polls a bounded device-side wait of this context's kernels makes before it
+   gives up (default 2^24, about a second): the waits of the TMA-staged
+   inner-row kernel (cfg.staging = 1) for its tiles.  A wait that gives up makes
+   its block wait (with the default bound) for its copies in flight and leave;
+   the next synchronising call returns LBM_ETIMEOUT and the state is not valid.
+   polls = 0 makes every such wait give up at once: a test of that failure path,
+   with no fault and no hang.  LBM_EINVAL for polls < 0.  The paper has no
+   counterpart. */
+lbm_status lbm_set_wait_limit(lbm_ctx* ctx, long long polls);
 
 /* Lattice parameters after unit conversion: out[0] = dt (s), out[1] = nu
    (lattice), out[2] = tau0, out[3..5] = F (lattice). */
@@ -244,33 +295,61 @@ lbm_status lbm_lattice_params(const lbm_ctx* ctx, double out[6]);
    calls (held on every GPU that loads the library until exit): lattices above
    16,777,216 cells are rejected with LBM_EINVAL, calls that overlap on the GPU
    race and must be serialised by the caller, and the first call on each device
-   looks up the array's address (make it before any stream capture).  Errors
-   are described by lbm_last_error(NULL). */
+   looks up the array's address (make it before any stream capture).  That
+   address is kept for the life of the process: after a cudaDeviceReset it is
+   stale, so do not call this entry point on a device that has been reset.
+   Devices with index >= 64 are rejected with LBM_EUNSUPPORTED.  Errors are
+   described by lbm_last_error(NULL). */
 lbm_status lbm_moments_noalloc(const void* f, int lattice, int storage, int nx, int ny, int nz,
                                int pitch, double* out, void* stream);
 
 /* ------------------------------------------------------------------------
- * Batched sweeps: many independent contexts advanced together by one
- * persistent, cooperative kernel launch per lbm_batch_step call (captured in
- * a CUDA graph).  Work items, each taken by one warp, are chunks of 32 wall
- * nodes or ranges of cells of one instance; a bounded grid barrier separates
- * the wall pre-pass and bulk phases of every step.
- * Instances keep their own configurations and boundary conditions; the
- * contexts must have been created and initialised (lbm_set_fields) first and
- * must share one stream.  The batch does not own the contexts.
+ * Batched sweeps (a mesh-sensitivity sweep of many channel and plate
+ * instances; the paper runs its grid and Reynolds-number studies of Sections
+ * 4.1.2.4 and 4.1.2.6 as separate runs).  Many independent contexts are
+ * advanced together by one persistent, cooperative kernel launch per
+ * lbm_batch_step call, replayed from a captured CUDA graph.  Work items, each
+ * taken by one warp in a fixed order from a ticket counter, are chunks of 32
+ * wall nodes (the wall pre-pass) and ranges of cells of one instance; an item
+ * waits only for the items of its own instance it depends on (the previous
+ * step, or this step's wall pre-pass for the wall rows), with bounded waits
+ * that report LBM_ETIMEOUT.  Each step of an instance computes what lbm_step
+ * computes.  Instances keep their own configurations and boundary conditions;
+ * the contexts must have been created and initialised (lbm_set_fields) first,
+ * must share one storage type and one stream, and are read back with
+ * lbm_fields / lbm_diagnostics.  The batch does not own the contexts; destroy
+ * it before them.
  * ---------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch;
 
+/* ctxs: n distinct contexts (host array, copied).  LBM_EINVAL for n < 1, NULL
+   or repeated contexts, a context without state or mixed storage types. */
 lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** out);
-/* Advance every instance by nsteps; the tile size (cells per work item, one
-   warp each) and threads per CTA are chosen by the built-in autotuner on the
-   first call unless lbm_batch_tune fixed them.  The autotuner advances every
-   instance while it times (24 steps). */
+/* Advance every instance by nsteps (enqueued on the contexts' stream; returns
+   without waiting for the GPU).  The tile size (cells per work item, one warp
+   each) and threads per CTA are chosen by the built-in autotuner on the first
+   call unless lbm_batch_tune fixed them; the autotuner advances every instance
+   while it times (24 steps).  A bounded wait of an earlier launch that gave up
+   is reported here (LBM_ETIMEOUT) once that launch has finished, or by
+   lbm_batch_wait; the instances' states are then not valid. */
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
 /* Time the candidate tile sizes (64, 256, 1024 cells per warp item) and block
    sizes (128, 256 threads) once and keep the fastest; best[0] = threads per
-   CTA, best[1] = cells per tile. */
+   CTA, best[1] = cells per tile (best may be NULL).  Synchronises. */
 lbm_status lbm_batch_tune(lbm_batch* b, int best[2]);
+/* Wait for the batch's launches to finish; LBM_ETIMEOUT if a bounded wait of
+   the last launch gave up. */
+lbm_status lbm_batch_wait(lbm_batch* b);
+/* Polls a waiting warp makes before it gives up (default 2^24, about a
+   second).  polls = 0 makes every wait that would have to poll give up at once
+   (every warp then leaves the kernel and lbm_batch_wait reports LBM_ETIMEOUT):
+   a test of that failure path, with no fault and no hang.  The paper has no
+   counterpart. */
+lbm_status lbm_batch_set_wait_limit(lbm_batch* b, long long polls);
+/* out[0] = threads per CTA, out[1] = cells per work item, out[2] = 1 if the
+   launches are replayed from a captured graph (0: launched directly because
+   capture was refused), out[3] = work items per step. */
+lbm_status lbm_batch_info(const lbm_batch* b, int out[4]);
 void lbm_batch_destroy(lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);
 

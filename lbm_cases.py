@@ -257,14 +257,16 @@ def flat_plate_2d(nx: int = 1100, ny: int = 250, dx: float = 2e-3,
 # Batched mesh-sensitivity sweep
 # ----------------------------------------------------------------------------
 
-def batched_sweep(n: int = 96, seed: int = 2506, storage: str = "fp32") -> List[Case]:
+def batched_sweep(n: int = 96, seed: int = 2506, storage: str = "fp32",
+                  plate_nx_cap: Optional[int] = None) -> List[Case]:
     """Heterogeneous instances for a mesh-sensitivity sweep.
 
     Instance k: D2Q9 if k is even else D3Q19 (nz = 4); channel if k % 3 != 2
     else flat plate; ny drawn from {16, ..., 256}; channel nx from {4, ..., 64}
     (D2Q9 channels use nx = 4), plate nx = min(4 ny, 1024); channel Re_tau
     log-uniform in [500, 2e4], plate Re per metre log-uniform in [1e6, 1e7];
-    slip-velocity bounce-back if k % 4 < 2 else HRFD.
+    slip-velocity bounce-back if k % 4 < 2 else HRFD.  ``plate_nx_cap`` caps the
+    plates' nx (same domain, coarser Delta) for parity runs of the same sweep.
     """
     rng = np.random.default_rng(seed)
     ny_choices = [16, 24, 32, 48, 64, 96, 128, 192, 256]
@@ -278,7 +280,7 @@ def batched_sweep(n: int = 96, seed: int = 2506, storage: str = "fp32") -> List[
         ny = int(rng.choice(ny_choices))
         if plate:
             re_m = float(np.exp(rng.uniform(np.log(1e6), np.log(1e7))))
-            nx = min(4 * ny, 1024)
+            nx = min(4 * ny, 1024, plate_nx_cap or 1024)
             u_inf = re_m * NU_AIR          # Re per metre = U / nu
             length = 2.048                 # domain length in metres
             dx = length / nx

@@ -26,7 +26,8 @@ __all__ = [
     "lbm_diagnostics", "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_destroy",
     "lbm_last_error", "lbm_lattice_params", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tune", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_moments_noalloc",
-    "lbm_kernel_launches", "lbm_run_to_convergence",
+    "lbm_kernel_launches", "lbm_run_to_convergence", "lbm_batch_wait", "lbm_batch_set_wait_limit",
+    "lbm_batch_info", "lbm_steps_done", "lbm_set_wait_limit",
 ]
 
 LIB_PATH = _build.LIB
@@ -127,6 +128,11 @@ def lib():
         "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
         "lbm_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+        "lbm_steps_done": (ctypes.c_longlong, [_P]),
+        "lbm_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
+        "lbm_batch_wait": (ctypes.c_int, [_P]),
+        "lbm_batch_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
+        "lbm_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -250,6 +256,34 @@ def lbm_batch_tune(b):
 
 def lbm_batch_destroy(b):
     lib().lbm_batch_destroy(b)
+
+
+def lbm_batch_wait(b) -> int:
+    """Raw status: LBM_OK, or LBM_ETIMEOUT if a bounded wait of the last launch gave up."""
+    return lib().lbm_batch_wait(b)
+
+
+def lbm_batch_set_wait_limit(b, polls: int):
+    st = lib().lbm_batch_set_wait_limit(b, int(polls))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_batch_set_wait_limit", lbm_batch_last_error(b))
+
+
+def lbm_batch_info(b):
+    """dict(threads, tile, use_graph, items_per_step) of a batch."""
+    out = (ctypes.c_int * 4)()
+    st = lib().lbm_batch_info(b, out)
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_batch_info", lbm_batch_last_error(b))
+    return dict(threads=out[0], tile=out[1], use_graph=bool(out[2]), items_per_step=out[3])
+
+
+def lbm_steps_done(ctx) -> int:
+    return int(lib().lbm_steps_done(ctx))
+
+
+def lbm_set_wait_limit(ctx, polls: int):
+    _check(lib().lbm_set_wait_limit(ctx, int(polls)), "lbm_set_wait_limit", ctx)
 
 
 def lbm_moments_noalloc(f_ptr, lattice: int, storage: int, nx: int, ny: int, nz: int,
@@ -400,6 +434,9 @@ class Solver:
 
     def kernel_launches(self) -> int:
         return lbm_kernel_launches(self.ctx)
+
+    def steps_done(self) -> int:
+        return lbm_steps_done(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

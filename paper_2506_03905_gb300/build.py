@@ -30,8 +30,23 @@ def nvcc() -> str:
     return exe
 
 
+# translation units compiled more than once, with one set of defines each
+# (inst.cu holds the step kernels' instantiations for one lattice)
+VARIANTS = {"inst.cu": [("inst_q9", ["-DLBM_Q=9"]), ("inst_q19", ["-DLBM_Q=19"])]}
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def _units():
+    """(source, object name, extra defines) of every translation unit."""
+    out = []
+    for src in _sources():
+        base = os.path.basename(src)
+        for name, defs in VARIANTS.get(base, [(base[:-3], [])]):
+            out.append((src, name, defs))
+    return out
 
 
 def _deps():
@@ -53,9 +68,10 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     exe = nvcc()
     extra = list(extra or [])
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [exe, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+    def compile_one(unit):
+        src, name, defs = unit
+        obj = os.path.join(BUILD, name + ".o")
+        cmd = [exe, *ARCH, *FLAGS, *defs, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -63,9 +79,9 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    units = _units()
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(units), os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = LIB + ".tmp"
     cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

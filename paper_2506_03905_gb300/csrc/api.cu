@@ -419,6 +419,7 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
     p.frec[b] = c->frec[b];
   }
   p.flags = c->flags;
+  p.wait_limit = c->wait_limit;
   // 1 / d^2 of the SA model per (y, x): distance to the nearest wall face (the
   // line d_w below row 0 / above row ny - 1), measured to the leading-edge
   // point for columns upstream of a wall's x_start; 0 without walls
@@ -677,6 +678,10 @@ static lbm_status ensure_graph(lbm_ctx* c, int parity) {
   return LBM_OK;
 }
 
+// Lattices with walls and at least this many cells launch their steps directly
+// (see lbm_step).
+constexpr long long kDirectWallCells = 1LL << 21;
+
 extern "C" lbm_status lbm_step(lbm_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return LBM_EINVAL;
   if (!c->ready) {
@@ -686,12 +691,14 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, int nsteps) {
   lbm_status s = lbm_ctx_finalize(c);
   if (s != LBM_OK) return s;
   int left = nsteps;
-  // Lattices with walls launch each step directly: the wall pre-pass branch
-  // only overlaps the inner rows when its stream priority is honoured, which
-  // replayed graphs did not do on GB300 (measured 0.38 ms vs 0.21 ms per step
-  // on the 256x128x128 channel).  Wall-free lattices replay captured graphs.
+  // Large lattices with walls launch each step directly: the wall pre-pass
+  // branch only overlaps the inner rows when its stream priority is honoured,
+  // which replayed graphs did not do on GB300 (measured 0.38 ms vs 0.21 ms per
+  // step on the 256x128x128 channel).  Smaller lattices, whose steps are bound
+  // by launch latency rather than by the overlap, and wall-free lattices replay
+  // captured graphs of two steps.
   const bool walls = c->base.wall[0] || c->base.wall[1];
-  if (walls) {
+  if (walls && c->ncells >= kDirectWallCells) {
     for (; left > 0; --left) {
       launch_step(c, c->cur, c->stream);
       c->cur ^= 1;
@@ -765,6 +772,7 @@ static lbm_status check_flags(lbm_ctx* c) {
   CUDA_TRY(c, cudaMemcpyAsync(h, c->flags, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->last_flags = h[0];
+  c->newton_count = h[1];
   if (h[0] & FLAG_TMA_TIMEOUT) {
     lbm_ctx_set_error(c, "a bounded wait for a tiled load expired; the state is not valid");
     return LBM_ETIMEOUT;
@@ -772,6 +780,11 @@ static lbm_status check_flags(lbm_ctx* c) {
   if (h[0] & FLAG_NONFINITE) {
     lbm_ctx_set_error(c, "non-finite value in the state");
     return LBM_ENONFINITE;
+  }
+  if (h[0] & FLAG_NEWTON) {
+    lbm_ctx_set_error(c, "the u_tau Newton iteration reached its limit at %u wall-node updates",
+                      h[1]);
+    return LBM_ENEWTON;
   }
   return LBM_OK;
 }
@@ -882,8 +895,9 @@ extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out) {
   out->mean_u_tau[1] = h[9] * vel;
   out->max_rel_du_tau = h[10];
   out->nonfinite = (c->last_flags & FLAG_NONFINITE) ? 1 : 0;
-  out->newton_failures = (c->last_flags & FLAG_NEWTON) ? 1 : 0;
-  return s == LBM_ENONFINITE ? LBM_OK : s;
+  out->newton_failures = (int)std::min<unsigned>(c->newton_count, 0x7fffffffu);
+  // non-finite values and Newton failures are reported in *out, not as errors
+  return (s == LBM_ENONFINITE || s == LBM_ENEWTON) ? LBM_OK : s;
 }
 
 extern "C" lbm_status lbm_run_to_convergence(lbm_ctx* c, double tol, int check_every,
@@ -997,4 +1011,14 @@ extern "C" void lbm_destroy(lbm_ctx* c) {
 
 extern "C" unsigned long long lbm_kernel_launches(const lbm_ctx* c) {
   return c ? c->launches : 0ULL;
+}
+
+extern "C" long long lbm_steps_done(const lbm_ctx* c) { return c ? c->steps_done : -1; }
+
+extern "C" lbm_status lbm_set_wait_limit(lbm_ctx* c, long long polls) {
+  if (!c || polls < 0) return LBM_EINVAL;
+  c->wait_limit = polls;
+  c->finalized = false;   // the limit is a kernel parameter: rebuild them (and the graphs)
+  c->gvalid[0] = c->gvalid[1] = false;
+  return LBM_OK;
 }

@@ -1,24 +1,39 @@
 // batch.cu -- batched sweeps: many independent lattices advanced by one
 // persistent, cooperative kernel launch (see include/lbm.h).
 //
-// Work is split into items: phase A items are chunks of wall nodes of one y
-// face of one instance, phase B items are ranges of cells of one instance.
-// Every warp of the persistent grid walks the item lists with a stride of the
-// number of warps in the grid; a grid barrier separates phase A (wall pre-pass of every
-// instance) from phase B (bulk update of every instance) and one step from
-// the next.  The barrier is an atomic counter with a generation number; its
-// spin is bounded (about a second), after which it records LBM_ETIMEOUT and
-// every CTA leaves the kernel.  The launch is cooperative, so all CTAs are
-// resident and the barrier cannot wait on a CTA that never starts.
+// Work is split into items, each taken by one warp: chunks of 32 wall nodes
+// of one y face of one instance (the wall pre-pass, kind A), ranges of cells
+// of the rows without wall nodes of one instance (kind B), and ranges of cells
+// of the wall rows of one instance (kind W, which read what the instance's A
+// items of the same step wrote).  The items of one step are listed as
+//   A items of every instance, then for each instance its B and W items,
+// and the steps of a launch follow one another.  Warps take items in that
+// order from one atomic ticket counter, so every item a warp may wait on has an
+// earlier ticket and is held by a running warp: no deadlock, and no grid-wide
+// barrier.  The dependencies are per instance and counted per instance:
+//   A(n, k) and B(n, k) need every item of step n-1 of instance k finished,
+//   W(n, k) needs every A item of step n of instance k finished,
+// which is what lets a warp start on one instance's next step while another
+// instance is still finishing its current one.  Every wait is bounded: after
+// spin_limit polls (about a second) the warp records a failure, and every warp
+// leaves at its next ticket or wait; the host reports LBM_ETIMEOUT.
 //
 // Each instance keeps its own configuration, faces and buffers (the Params of
 // its context for both buffer parities); only the storage type has to be the
 // same for all instances of a batch.  The instances' buffer parities live in
-// device memory and are advanced by the kernel, so a captured launch can be
-// replayed without host updates.
+// device memory and are advanced by the warp that finishes an instance's last
+// item of the launch, so a captured launch can be replayed without host
+// updates.  The counters are cleared by a memset captured with the launch.
+//
+// This translation unit reads, within one launch, data that other warps wrote
+// earlier in the same launch; it defines LBM_COHERENT_LOADS so that those
+// loads are plain global loads, ordered by the fences around the counters.
+#define LBM_COHERENT_LOADS 1
+
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -35,54 +50,57 @@ struct BatchInst {
   Params p[2];   // p[k]: step reading buffer k
   int Q;
   int cur;       // buffer the next step reads (advanced by the kernel)
-  int nx, ny, nz;
+  int items;     // work items of one step
+  int itemsA;    // wall pre-pass items of one step
 };
+
+enum { KIND_A = 0, KIND_B = 1, KIND_W = 2 };
 
 struct WorkItem {
   int inst;
-  int face;      // phase A: 0 = ymin, 1 = ymax
-  int begin, end;
+  int kind;      // KIND_A / KIND_B / KIND_W
+  int face;      // KIND_A: 0 = ymin, 1 = ymax
+  int begin, end;   // wall nodes (A) or cells of the item's row set (B, W)
+  int pad[2];
 };
 
-struct GridBar {
-  unsigned count;
-  unsigned gen;
+// Control block of one launch, cleared before it: the ticket counter, the
+// failure flag, then per instance the finished items and finished A items.
+struct BatchCtl {
+  unsigned long long next;
   unsigned err;
   unsigned pad;
 };
 
 constexpr long long kSpinLimit = 1LL << 24;   // x ~64 ns sleep: about one second
 
-// Grid-wide barrier of a cooperative launch; returns false once any CTA gave up.
-__device__ bool grid_sync(GridBar* bar) {
-  __shared__ int ok_sh;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &bar->gen;
-    const unsigned g = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&bar->count, 1u);
-    int ok = 1;
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      long long it = 0;
-      while (*vgen == g) {
-        if (++it > kSpinLimit) {
-          atomicOr(&bar->err, 1u);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
+// Lane 0 waits until *ctr >= target; false if the wait gave up or another warp
+// already failed.  spin_limit == 0 is the test setting: every wait that would
+// have to poll at all gives up at once.
+__device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target, BatchCtl* ctl,
+                                           long long spin_limit, int lane) {
+  int ok = 1;
+  if (lane == 0 && target > 0) {
+    volatile const unsigned* v = ctr;
+    volatile const unsigned* verr = &ctl->err;
+    long long it = 0;
+    while (*v < target) {
+      if (*verr) {
+        ok = 0;
+        break;
       }
+      if (++it > spin_limit) {
+        atomicOr(&ctl->err, 1u);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
     }
-    __threadfence();
-    ok_sh = ok && (atomicAdd(&bar->err, 0u) == 0u);
+    __threadfence();   // acquire: the producers' writes are visible after this
   }
-  __syncthreads();
-  return ok_sh != 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
 }
 
 // Work items are taken by warps: each warp copies the parameters of its
@@ -93,21 +111,18 @@ __device__ bool grid_sync(GridBar* bar) {
 // item holds up no other warp of the CTA.
 constexpr int kMaxWarps = 8;   // blocks of at most 256 threads
 
-__device__ __forceinline__ void warp_load_params(Params* dst, const Params* src, int* q_dst,
-                                                 const int* q_src, int lane) {
+__device__ __forceinline__ void warp_load_params(Params* dst, const Params* src, int lane) {
   static_assert(sizeof(Params) % sizeof(int) == 0, "Params is copied as ints");
   __syncwarp();      // the warp is done with its previous item's copy
   const int* s = reinterpret_cast<const int*>(src);
   int* d = reinterpret_cast<int*>(dst);
   for (int k = lane; k < (int)(sizeof(Params) / sizeof(int)); k += 32) d[k] = s[k];
-  if (lane == 0) *q_dst = *q_src;
   __syncwarp();
 }
 
 // Minimum resident blocks per SM requested from the compiler for k_batch (its
 // register budget; 0 leaves the choice to the compiler).  Three blocks of 256
-// (<= 80 registers, a few spilled) measured fastest on GB300 for the 96-instance
-// sweep.
+// (<= 80 registers) measured fastest on GB300 for the 96-instance sweep.
 #ifndef LBM_BATCH_MINB
 #define LBM_BATCH_MINB 3
 #endif
@@ -117,50 +132,75 @@ __device__ __forceinline__ void warp_load_params(Params* dst, const Params* src,
 #define LBM_BATCH_BOUNDS __launch_bounds__(256)
 #endif
 
+// Cell (x, y, z) of entry c of an item's row set: B covers rows 1..ny-2 of an
+// instance with walls (every row without), W covers rows 0 and ny-1.
+__device__ __forceinline__ void item_cell(const Params& p, int kind, bool walls, int c, int* x,
+                                          int* y, int* z) {
+  const int nx = p.nx;
+  const int nrow = kind == KIND_W ? 2 : (walls ? p.ny - 2 : p.ny);
+  const int per_z = nx * nrow;
+  *z = c / per_z;
+  const int r = c - *z * per_z;
+  const int j = r / nx;
+  *x = r - j * nx;
+  *y = kind == KIND_W ? (j == 0 ? 0 : p.ny - 1) : (walls ? j + 1 : j);
+}
+
 template <int ST>
-__global__ void LBM_BATCH_BOUNDS k_batch(BatchInst* inst, int ninst, const WorkItem* itemsA,
-                               int nA, const WorkItem* itemsB, int nB, GridBar* bar, int nsteps) {
+__global__ void LBM_BATCH_BOUNDS k_batch(BatchInst* inst, const WorkItem* items, int nitems,
+                                         BatchCtl* ctl, unsigned* done, unsigned* done_a,
+                                         int nsteps, long long spin_limit) {
   __shared__ Params sp[kMaxWarps];
-  __shared__ int sq[kMaxWarps];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + wib, nw = gridDim.x * (blockDim.x >> 5);
-  for (int step = 0; step < nsteps; ++step) {
-    // phase A: wall pre-pass of every instance (items of 32 wall nodes)
-    for (int it = gw; it < nA; it += nw) {
-      const WorkItem w = itemsA[it];
-      const BatchInst& b = inst[w.inst];
-      warp_load_params(&sp[wib], &b.p[(b.cur + step) & 1], &sq[wib], &b.Q, lane);
-      const Params& p = sp[wib];
-      const int Q = sq[wib];
+  const unsigned long long total = (unsigned long long)nsteps * (unsigned long long)nitems;
+  volatile const unsigned* verr = &ctl->err;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = *verr ? total : atomicAdd(&ctl->next, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= total) break;
+    const int step = (int)(t / (unsigned long long)nitems);
+    const WorkItem w = items[(int)(t - (unsigned long long)step * nitems)];
+    BatchInst& b = inst[w.inst];
+    const unsigned per = (unsigned)b.items, per_a = (unsigned)b.itemsA;
+    // dependencies of this item (every counted item has an earlier ticket)
+    const bool ok = w.kind == KIND_W
+                        ? wait_count(&done_a[w.inst], spin_limit == 0 ? ~0u : (step + 1) * per_a, ctl,
+                                     spin_limit, lane)
+                        : wait_count(&done[w.inst],
+                                     step == 0 ? 0u : (spin_limit == 0 ? ~0u : step * per), ctl,
+                                     spin_limit, lane);
+    if (!ok) break;
+    warp_load_params(&sp[wib], &b.p[(b.cur + step) & 1], lane);
+    const Params& p = sp[wib];
+    const int Q = b.Q;
+    if (w.kind == KIND_A) {
       for (int node = w.begin + lane; node < w.end; node += 32) {
         if (Q == 19) wall_node<19, ST>(p, w.face, node);
         else wall_node<9, ST>(p, w.face, node);
       }
-    }
-    if (!grid_sync(bar)) return;
-    // phase B: bulk update of every cell of every instance
-    for (int it = gw; it < nB; it += nw) {
-      const WorkItem w = itemsB[it];
-      const BatchInst& b = inst[w.inst];
-      warp_load_params(&sp[wib], &b.p[(b.cur + step) & 1], &sq[wib], &b.Q, lane);
-      const Params& p = sp[wib];
-      const int Q = sq[wib], nx = p.nx, nxy = p.nx * p.ny;
+    } else {
+      const bool walls = per_a > 0;
       for (int c = w.begin + lane; c < w.end; c += 32) {
-        const int z = c / nxy, r = c - z * nxy;
-        const int y = r / nx, x = r - y * nx;
+        int x, y, z;
+        item_cell(p, w.kind, walls, c, &x, &y, &z);
         if (Q == 19) bulk_cell<19, ST, true>(p, x, y, z);
         else bulk_cell<9, ST, true>(p, x, y, z);
       }
     }
-    if (!grid_sync(bar)) return;
-  }
-  if (blockIdx.x == 0) {
-    for (int i = threadIdx.x; i < ninst; i += blockDim.x) inst[i].cur = (inst[i].cur + nsteps) & 1;
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();   // release: this item's writes before its count
+      if (w.kind == KIND_A) atomicAdd(&done_a[w.inst], 1u);
+      const unsigned d = atomicAdd(&done[w.inst], 1u) + 1u;
+      // the instance's last item of this launch: no other item of it remains
+      if (d == (unsigned)nsteps * per) b.cur = (b.cur + nsteps) & 1;
+    }
   }
 }
 
-using BatchKernel = void (*)(BatchInst*, int, const WorkItem*, int, const WorkItem*, int, GridBar*,
-                             int);
+using BatchKernel = void (*)(BatchInst*, const WorkItem*, int, BatchCtl*, unsigned*, unsigned*, int,
+                             long long);
 
 BatchKernel batch_kernel(int st) {
   switch (st) {
@@ -180,20 +220,23 @@ struct lbm_batch {
   int st = 0;
   cudaStream_t stream = nullptr;
   BatchInst* d_inst = nullptr;
-  GridBar* d_bar = nullptr;
-  WorkItem* d_itemsA = nullptr;
-  int nA = 0;
-  WorkItem* d_itemsB = nullptr;
-  int nB = 0;
+  std::vector<BatchInst> h_inst;
+  WorkItem* d_items = nullptr;
+  int nitems = 0;                // items of one step
+  void* d_ctl = nullptr;         // BatchCtl, then done[n], done_a[n]
+  size_t ctl_bytes = 0;
   int threads = 256;
-  int tile = 256;         // cells per phase-B item (one warp each)
+  int tile = 256;                // cells per B / W item (one warp each)
   int grid = 0;
   bool tuned = false;
-  bool launched = false;  // a launch may still be running: check its barrier flag first
-  bool use_graph = true;  // false if capturing the cooperative launch was refused
+  bool use_graph = true;         // false if capturing the cooperative launch was refused
   cudaGraphExec_t gexec = nullptr;
   int g_nsteps = -1;
-  std::vector<int> dev_cur;  // buffer parity of each instance as the device holds it
+  std::vector<int> dev_cur;      // buffer parity of each instance as the device holds it
+  long long spin_limit = kSpinLimit;   // polls before a warp gives up at a wait
+  BatchCtl* h_ctl = nullptr;     // pinned copy of the control block after each launch
+  cudaEvent_t ev_ctl = nullptr;
+  bool ctl_pending = false;      // a launch's control copy has not been inspected yet
   std::string err;
 };
 
@@ -206,6 +249,13 @@ struct lbm_batch {
     }                                                                        \
   } while (0)
 
+static void drop_graph(lbm_batch* b) {
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+}
+
 // Instances in work-item order: D3Q19 first, then D2Q9, so that the warps of
 // an SM mostly run one lattice's code at a time (instruction-cache locality).
 static std::vector<int> instance_order(const lbm_batch* b) {
@@ -216,45 +266,58 @@ static std::vector<int> instance_order(const lbm_batch* b) {
   return order;
 }
 
-// Phase B items: ranges of `tile` cells of one instance, each advanced by one warp.
-static lbm_status build_items_B(lbm_batch* b, int tile) {
+// The items of one step: wall-node chunks of 32 of every instance first, then
+// per instance its ranges of `tile` cells of the rows without wall nodes and of
+// the wall rows.
+static lbm_status build_items(lbm_batch* b, int tile) {
   std::vector<WorkItem> items;
-  for (int i : instance_order(b)) {
-    const lbm_ctx* c = b->ctxs[i];
-    const int n = (int)c->ncells;
-    for (int a = 0; a < n; a += tile) items.push_back({i, 0, a, std::min(n, a + tile)});
-  }
-  if (b->d_itemsB) cudaFree(b->d_itemsB);
-  b->d_itemsB = nullptr;
-  b->nB = (int)items.size();
-  BATCH_TRY(b, cudaMalloc(&b->d_itemsB, std::max<size_t>(1, items.size()) * sizeof(WorkItem)));
-  BATCH_TRY(b, cudaMemcpy(b->d_itemsB, items.data(), items.size() * sizeof(WorkItem),
-                          cudaMemcpyHostToDevice));
-  b->tile = tile;
-  if (b->gexec) {
-    cudaGraphExecDestroy(b->gexec);
-    b->gexec = nullptr;
-  }
-  return LBM_OK;
-}
-
-// Phase A items: chunks of one warp of wall nodes of one face of one instance.
-static lbm_status build_items_A(lbm_batch* b, int chunk) {
-  std::vector<WorkItem> items;
-  for (int i : instance_order(b)) {
+  const std::vector<int> order = instance_order(b);
+  std::vector<int> per(b->ctxs.size(), 0), per_a(b->ctxs.size(), 0);
+  for (int i : order) {
     const lbm_ctx* c = b->ctxs[i];
     for (int f = 0; f < 2; ++f) {
       if (!c->base.wall[f]) continue;
       const int nw = c->base.nwall[f];
-      for (int a = 0; a < nw; a += chunk) items.push_back({i, f, a, std::min(nw, a + chunk)});
+      for (int a = 0; a < nw; a += 32) {
+        items.push_back({i, KIND_A, f, a, std::min(nw, a + 32), {0, 0}});
+        ++per_a[i];
+      }
     }
   }
-  if (b->d_itemsA) cudaFree(b->d_itemsA);
-  b->d_itemsA = nullptr;
-  b->nA = (int)items.size();
-  BATCH_TRY(b, cudaMalloc(&b->d_itemsA, std::max<size_t>(1, items.size()) * sizeof(WorkItem)));
-  BATCH_TRY(b, cudaMemcpy(b->d_itemsA, items.data(), items.size() * sizeof(WorkItem),
+  for (int i : order) {
+    const lbm_ctx* c = b->ctxs[i];
+    const bool walls = per_a[i] > 0;
+    const int nb = c->nx * c->nz * (walls ? c->ny - 2 : c->ny);
+    for (int a = 0; a < nb; a += tile) items.push_back({i, KIND_B, 0, a, std::min(nb, a + tile), {0, 0}});
+    if (walls) {
+      const int nwr = 2 * c->nx * c->nz;
+      for (int a = 0; a < nwr; a += tile)
+        items.push_back({i, KIND_W, 0, a, std::min(nwr, a + tile), {0, 0}});
+    }
+  }
+  for (const WorkItem& w : items) ++per[w.inst];
+  if (b->d_items) cudaFree(b->d_items);
+  b->d_items = nullptr;
+  b->nitems = (int)items.size();
+  BATCH_TRY(b, cudaMalloc(&b->d_items, std::max<size_t>(1, items.size()) * sizeof(WorkItem)));
+  BATCH_TRY(b, cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem),
                           cudaMemcpyHostToDevice));
+  // per-instance item counts, written into the two adjacent int fields of each
+  // device instance record (its parity is left as the device holds it); no
+  // launch is in flight when the items are rebuilt
+  std::vector<int> counts(2 * b->ctxs.size());
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    counts[2 * i] = per[i];
+    counts[2 * i + 1] = per_a[i];
+  }
+  static_assert(offsetof(BatchInst, itemsA) == offsetof(BatchInst, items) + sizeof(int),
+                "items and itemsA are adjacent");
+  BATCH_TRY(b, cudaMemcpy2DAsync((char*)b->d_inst + offsetof(BatchInst, items), sizeof(BatchInst),
+                                 counts.data(), 2 * sizeof(int), 2 * sizeof(int), b->ctxs.size(),
+                                 cudaMemcpyHostToDevice, b->stream));
+  BATCH_TRY(b, cudaStreamSynchronize(b->stream));
+  b->tile = tile;
+  drop_graph(b);
   return LBM_OK;
 }
 
@@ -269,17 +332,14 @@ static lbm_status set_threads(lbm_batch* b, int threads) {
   }
   b->threads = threads;
   b->grid = sms * per_sm;
-  lbm_status s = build_items_A(b, 32);
-  if (s != LBM_OK) return s;
-  if (b->gexec) {
-    cudaGraphExecDestroy(b->gexec);
-    b->gexec = nullptr;
-  }
+  drop_graph(b);
   return LBM_OK;
 }
 
-// Enqueue one cooperative launch advancing every instance by nsteps.
+// Enqueue the control-block reset and one cooperative launch advancing every
+// instance by nsteps.
 static lbm_status launch(lbm_batch* b, int nsteps, cudaStream_t s) {
+  BATCH_TRY(b, cudaMemsetAsync(b->d_ctl, 0, b->ctl_bytes, s));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->grid, 1, 1);
   cfg.blockDim = dim3(b->threads, 1, 1);
@@ -290,18 +350,43 @@ static lbm_status launch(lbm_batch* b, int nsteps, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  BATCH_TRY(b, cudaLaunchKernelEx(&cfg, batch_kernel(b->st), b->d_inst, (int)b->ctxs.size(),
-                                  (const WorkItem*)b->d_itemsA, b->nA,
-                                  (const WorkItem*)b->d_itemsB, b->nB, b->d_bar, nsteps));
+  BatchCtl* ctl = (BatchCtl*)b->d_ctl;
+  unsigned* done = (unsigned*)((char*)b->d_ctl + sizeof(BatchCtl));
+  unsigned* done_a = done + b->ctxs.size();
+  BATCH_TRY(b, cudaLaunchKernelEx(&cfg, batch_kernel(b->st), b->d_inst,
+                                  (const WorkItem*)b->d_items, b->nitems, ctl, done, done_a, nsteps,
+                                  b->spin_limit));
   return LBM_OK;
 }
 
-static lbm_status check_bar(lbm_batch* b) {
-  GridBar h;
-  BATCH_TRY(b, cudaMemcpyAsync(&h, b->d_bar, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
-  BATCH_TRY(b, cudaStreamSynchronize(b->stream));
-  if (h.err) {
-    b->err = "grid barrier of the batch kernel timed out";
+// After a launch on b->stream: copy the control block to pinned host memory
+// behind it, to be inspected later without blocking the host.
+static lbm_status queue_ctl_copy(lbm_batch* b) {
+  BATCH_TRY(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost,
+                               b->stream));
+  BATCH_TRY(b, cudaEventRecord(b->ev_ctl, b->stream));
+  b->ctl_pending = true;
+  return LBM_OK;
+}
+
+// Inspect the control copy of the last launch.  blocking = false: if that
+// launch has not finished yet, report nothing now (a later call will).  After
+// a reported timeout the instances' states are not valid; the device parities
+// are re-sent before the next launch.
+static lbm_status poll_ctl(lbm_batch* b, bool blocking) {
+  if (!b->ctl_pending) return LBM_OK;
+  if (blocking) {
+    BATCH_TRY(b, cudaEventSynchronize(b->ev_ctl));
+  } else {
+    const cudaError_t q = cudaEventQuery(b->ev_ctl);
+    if (q == cudaErrorNotReady) return LBM_OK;
+    BATCH_TRY(b, q);
+  }
+  b->ctl_pending = false;
+  if (b->h_ctl->err) {
+    b->h_ctl->err = 0;
+    for (int& d : b->dev_cur) d = -1;
+    b->err = "a bounded wait of the batch kernel gave up; the instances' states are not valid";
     return LBM_ETIMEOUT;
   }
   return LBM_OK;
@@ -312,7 +397,7 @@ static void advance_host_parity(lbm_batch* b, int nsteps) {
     lbm_ctx* c = b->ctxs[i];
     c->cur = (c->cur + nsteps) & 1;
     c->steps_done += nsteps;
-    b->dev_cur[i] = (b->dev_cur[i] + nsteps) & 1;
+    if (b->dev_cur[i] >= 0) b->dev_cur[i] = (b->dev_cur[i] + nsteps) & 1;
   }
 }
 
@@ -328,6 +413,14 @@ static lbm_status sync_parity(lbm_batch* b) {
     b->dev_cur[i] = cur;
   }
   return LBM_OK;
+}
+
+// One launch of nsteps on b->stream (directly), with its control copy.
+static lbm_status launch_tracked(lbm_batch* b, int nsteps) {
+  lbm_status s = launch(b, nsteps, b->stream);
+  if (s != LBM_OK) return s;
+  advance_host_parity(b, nsteps);
+  return queue_ctl_copy(b);
 }
 
 extern "C" lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** out) {
@@ -356,41 +449,48 @@ extern "C" lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** 
       g_batch_err = "lbm_batch_create: all instances must share one storage type";
       return LBM_EINVAL;
     }
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) {
+        delete b;
+        g_batch_err = "lbm_batch_create: a context appears twice";
+        return LBM_EINVAL;
+      }
     b->ctxs.push_back(c);
   }
   b->st = ctxs[0]->st;
   b->stream = ctxs[0]->stream;
   for (int i = 0; i < n; ++i) b->dev_cur.push_back(ctxs[i]->cur);
-  std::vector<BatchInst> hi(n);
+  b->h_inst.resize(n);
   for (int i = 0; i < n; ++i) {
     const lbm_ctx* c = ctxs[i];
-    std::memset(&hi[i], 0, sizeof(BatchInst));
-    hi[i].p[0] = lbm_ctx_params(c, 0);
-    hi[i].p[1] = lbm_ctx_params(c, 1);
-    hi[i].Q = c->Q;
-    hi[i].cur = c->cur;
-    hi[i].nx = c->nx;
-    hi[i].ny = c->ny;
-    hi[i].nz = c->nz;
+    std::memset(&b->h_inst[i], 0, sizeof(BatchInst));
+    b->h_inst[i].p[0] = lbm_ctx_params(c, 0);
+    b->h_inst[i].p[1] = lbm_ctx_params(c, 1);
+    b->h_inst[i].Q = c->Q;
+    b->h_inst[i].cur = c->cur;
   }
-  lbm_status st = LBM_OK;
+  b->ctl_bytes = sizeof(BatchCtl) + 2 * (size_t)n * sizeof(unsigned);
   if (cudaMalloc(&b->d_inst, n * sizeof(BatchInst)) != cudaSuccess ||
-      cudaMalloc(&b->d_bar, sizeof(GridBar)) != cudaSuccess) {
+      cudaMalloc(&b->d_ctl, b->ctl_bytes) != cudaSuccess ||
+      cudaMallocHost(&b->h_ctl, sizeof(BatchCtl)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_ctl, cudaEventDisableTiming) != cudaSuccess) {
     g_batch_err = "lbm_batch_create: device allocation failed";
     lbm_batch_destroy(b);
     return LBM_ENOMEM;
   }
+  std::memset(b->h_ctl, 0, sizeof(BatchCtl));
   // the contexts' pending work (state set-up) must be complete before the batch
   // reads their parameters on another order of launches
   for (lbm_ctx* c : b->ctxs) cudaStreamSynchronize(c->stream);
-  if (cudaMemcpy(b->d_inst, hi.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(b->d_bar, 0, sizeof(GridBar)) != cudaSuccess) {
+  if (cudaMemcpy(b->d_inst, b->h_inst.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemset(b->d_ctl, 0, b->ctl_bytes) != cudaSuccess) {
     g_batch_err = "lbm_batch_create: upload failed";
     lbm_batch_destroy(b);
     return LBM_ECUDA;
   }
-  st = set_threads(b, 256);
-  if (st == LBM_OK) st = build_items_B(b, 256);
+  lbm_status st = set_threads(b, 256);
+  if (st == LBM_OK) st = build_items(b, 256);
   if (st != LBM_OK) {
     g_batch_err = b->err;
     lbm_batch_destroy(b);
@@ -404,10 +504,10 @@ extern "C" lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** 
 // advances every instance by its steps) and the fastest pair is kept.
 extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int best[2]) {
   if (!b) return LBM_EINVAL;
-  {
-    lbm_status s0 = sync_parity(b);
-    if (s0 != LBM_OK) return s0;
-  }
+  lbm_status s = poll_ctl(b, true);
+  if (s != LBM_OK) return s;
+  s = sync_parity(b);
+  if (s != LBM_OK) return s;
   const int threads_c[2] = {128, 256};
   const int tiles_c[3] = {64, 256, 1024};   // cells per warp item
   float best_ms = 1e30f;
@@ -417,20 +517,19 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int best[2]) {
   BATCH_TRY(b, cudaEventCreate(&e1));
   const int trial = 3;
   for (int t : threads_c) {
-    lbm_status s = set_threads(b, t);
+    s = set_threads(b, t);
     if (s != LBM_OK) continue;
     for (int k : tiles_c) {
-      s = build_items_B(b, k);
-      if (s != LBM_OK) return s;
-      s = launch(b, 1, b->stream);   // warm-up
-      if (s != LBM_OK) return s;
-      advance_host_parity(b, 1);
+      s = build_items(b, k);
+      if (s == LBM_OK) s = launch_tracked(b, 1);   // warm-up
+      if (s != LBM_OK) break;
       BATCH_TRY(b, cudaEventRecord(e0, b->stream));
-      s = launch(b, trial, b->stream);
-      if (s != LBM_OK) return s;
-      advance_host_parity(b, trial);
+      s = launch_tracked(b, trial);
+      if (s != LBM_OK) break;
       BATCH_TRY(b, cudaEventRecord(e1, b->stream));
       BATCH_TRY(b, cudaEventSynchronize(e1));
+      s = poll_ctl(b, true);
+      if (s != LBM_OK) break;
       float ms = 0.f;
       BATCH_TRY(b, cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best_ms) {
@@ -439,48 +538,38 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int best[2]) {
         btile = k;
       }
     }
+    if (s != LBM_OK && s != LBM_EUNSUPPORTED) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  lbm_status s = set_threads(b, bt);
-  if (s == LBM_OK) s = build_items_B(b, btile);
+  if (s != LBM_OK && s != LBM_EUNSUPPORTED) return s;
+  s = set_threads(b, bt);
+  if (s == LBM_OK) s = build_items(b, btile);
   if (s != LBM_OK) return s;
   b->tuned = true;
   if (best) {
     best[0] = bt;
     best[1] = btile;
   }
-  return check_bar(b);
+  return LBM_OK;
 }
 
 extern "C" lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
   if (!b || nsteps < 0) return LBM_EINVAL;
   if (nsteps == 0) return LBM_OK;
-  lbm_status s;
-  if (b->launched) {
-    // a barrier timeout of the previous launch is reported here
-    s = check_bar(b);
-    if (s != LBM_OK) return s;
-  }
+  // a timeout of an earlier launch that has finished is reported here
+  lbm_status s = poll_ctl(b, false);
+  if (s != LBM_OK) return s;
   s = sync_parity(b);
   if (s != LBM_OK) return s;
   if (!b->tuned) {
     s = lbm_batch_tune(b, nullptr);
     if (s != LBM_OK) return s;
   }
-  if (!b->use_graph) {
-    s = launch(b, nsteps, b->stream);
-    if (s != LBM_OK) return s;
-    advance_host_parity(b, nsteps);
-    b->launched = true;
-    return LBM_OK;
-  }
+  if (!b->use_graph) return launch_tracked(b, nsteps);
   // one persistent launch per call, replayed from a graph while nsteps repeats
   if (!b->gexec || b->g_nsteps != nsteps) {
-    if (b->gexec) {
-      cudaGraphExecDestroy(b->gexec);
-      b->gexec = nullptr;
-    }
+    drop_graph(b);
     cudaStream_t cap;
     BATCH_TRY(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
@@ -492,32 +581,53 @@ extern "C" lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
     }
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cap);
-    if (e != cudaSuccess || !b->gexec) {
+    if (e != cudaSuccess || s != LBM_OK || !b->gexec) {
       // the cooperative launch could not be captured: launch it directly
       cudaGetLastError();
+      drop_graph(b);
       b->use_graph = false;
-      s = launch(b, nsteps, b->stream);
-      if (s != LBM_OK) return s;
-      advance_host_parity(b, nsteps);
-      b->launched = true;
-      return LBM_OK;
+      return launch_tracked(b, nsteps);
     }
     b->g_nsteps = nsteps;
   }
   BATCH_TRY(b, cudaGraphLaunch(b->gexec, b->stream));
   advance_host_parity(b, nsteps);
-  b->launched = true;
+  return queue_ctl_copy(b);
+}
+
+extern "C" lbm_status lbm_batch_wait(lbm_batch* b) {
+  if (!b) return LBM_EINVAL;
+  lbm_status s = poll_ctl(b, true);
+  if (s != LBM_OK) return s;
+  BATCH_TRY(b, cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_set_wait_limit(lbm_batch* b, long long polls) {
+  if (!b || polls < 0) return LBM_EINVAL;
+  b->spin_limit = polls > 0 ? polls : 0;
+  drop_graph(b);   // the limit is a launch argument of the captured kernel
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_info(const lbm_batch* b, int out[4]) {
+  if (!b || !out) return LBM_EINVAL;
+  out[0] = b->threads;
+  out[1] = b->tile;
+  out[2] = b->use_graph ? 1 : 0;
+  out[3] = b->nitems;
   return LBM_OK;
 }
 
 extern "C" void lbm_batch_destroy(lbm_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
-  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  drop_graph(b);
   if (b->d_inst) cudaFree(b->d_inst);
-  if (b->d_bar) cudaFree(b->d_bar);
-  if (b->d_itemsA) cudaFree(b->d_itemsA);
-  if (b->d_itemsB) cudaFree(b->d_itemsB);
+  if (b->d_ctl) cudaFree(b->d_ctl);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->h_ctl) cudaFreeHost(b->h_ctl);
+  if (b->ev_ctl) cudaEventDestroy(b->ev_ctl);
   delete b;
 }
 

@@ -1,6 +1,18 @@
-// Template instantiations of the step kernels for the D2Q9 lattice (all storage types).
+// Template instantiations of the step kernels for one lattice (all storage
+// types).  The build compiles this file once per lattice with -DLBM_Q=9 and
+// -DLBM_Q=19; the launchers it defines are named launch_*_q9 / launch_*_q19.
+#ifndef LBM_Q
+#error "compile with -DLBM_Q=9 or -DLBM_Q=19"
+#endif
+#if LBM_Q != 9 && LBM_Q != 19
+#error "LBM_Q must be 9 or 19"
+#endif
 #include "lbm_kernels.cuh"
 #include "lbm_launch.h"
+
+#define LBM_QCAT2(a, b) a##_q##b
+#define LBM_QCAT(a, b) LBM_QCAT2(a, b)
+#define LBM_QNAME(fn) LBM_QCAT(fn, LBM_Q)
 
 namespace lbm {
 
@@ -31,16 +43,16 @@ static void launch_prio(void (*k)(A...), dim3 g, dim3 b, cudaStream_t s, int pri
 // shared memory.
 template <int ST>
 static void bulk_tma_st(const Params& p, const CUtensorMap& tm, int zchunk, cudaStream_t s) {
-  using TT = TmaTile<9, ST>;
+  using TT = TmaTile<LBM_Q, ST>;
   const int smem = TT::SMEM_BYTES;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_bulk_tma<9, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_bulk_tma<LBM_Q, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr_set = true;
   }
   dim3 g((p.nx + 31) / 32, (p.ny - 2 + TT::BH - 1) / TT::BH, (p.nz + zchunk - 1) / zchunk);
   dim3 b(32, TT::BH, 1);
-  k_bulk_tma<9, ST><<<g, b, smem, s>>>(p, tm, zchunk);
+  k_bulk_tma<LBM_Q, ST><<<g, b, smem, s>>>(p, tm, zchunk);
 }
 
 template <int ST>
@@ -50,12 +62,12 @@ static void bulk_st(const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, i
   // non-periodic x axis go to a separate ROWS_XEDGE launch), or every row of
   // a lattice periodic in x and y
   const bool fast = rows == ROWS_INNER || (rows == ROWS_ALL && p.px && p.py);
-  if (fast) launch_prio(k_bulk<9, ST, false>, g, b, s, prio, p, rows);
-  else launch_prio(k_bulk<9, ST, true>, g, b, s, prio, p, rows);
+  if (fast) launch_prio(k_bulk<LBM_Q, ST, false>, g, b, s, prio, p, rows);
+  else launch_prio(k_bulk<LBM_Q, ST, true>, g, b, s, prio, p, rows);
 }
 template <int ST>
 static void wall_st(const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
-  launch_prio(k_wall<9, ST>, g, b, s, prio, p);
+  launch_prio(k_wall<LBM_Q, ST>, g, b, s, prio, p);
 }
 
 #define LBM_DISPATCH(FN, ...)                       \
@@ -66,22 +78,22 @@ static void wall_st(const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
     default: FN<ST_FP64>(__VA_ARGS__); break;       \
   }
 
-void launch_bulk_q9(int st, const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, int prio) {
+void LBM_QNAME(launch_bulk)(int st, const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, int prio) {
   LBM_DISPATCH(bulk_st, p, rows, g, b, s, prio)
 }
-void launch_bulk_tma_q9(int st, const Params& p, const CUtensorMap& tm, int zchunk, cudaStream_t s) {
+void LBM_QNAME(launch_bulk_tma)(int st, const Params& p, const CUtensorMap& tm, int zchunk, cudaStream_t s) {
   LBM_DISPATCH(bulk_tma_st, p, tm, zchunk, s)
 }
-void launch_wall_q9(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
+void LBM_QNAME(launch_wall)(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
   LBM_DISPATCH(wall_st, p, g, b, s, prio)
 }
 
 template <int ST>
 static void init_st(const Params& p, int grid, const double* rho, const double* u,
                     const double* nt, double rho0, double ucv, double nucv, cudaStream_t s) {
-  k_init<9, ST><<<grid, 256, 0, s>>>(p, rho, u, nt, rho0, ucv, nucv);
+  k_init<LBM_Q, ST><<<grid, 256, 0, s>>>(p, rho, u, nt, rho0, ucv, nucv);
 }
-void launch_init_q9(int st, const Params& p, int grid, const double* rho, const double* u,
+void LBM_QNAME(launch_init)(int st, const Params& p, int grid, const double* rho, const double* u,
                      const double* nt, double rho0, double ucv, double nucv, cudaStream_t s) {
   LBM_DISPATCH(init_st, p, grid, rho, u, nt, rho0, ucv, nucv, s)
 }
@@ -89,18 +101,18 @@ void launch_init_q9(int st, const Params& p, int grid, const double* rho, const 
 template <int ST>
 static void fields_st(const Params& p, int grid, double* rho, double* u, double* nut, double* nt,
                       double rho0, double vel, double visc, cudaStream_t s) {
-  k_fields<9, ST><<<grid, 256, 0, s>>>(p, rho, u, nut, nt, rho0, vel, visc);
+  k_fields<LBM_Q, ST><<<grid, 256, 0, s>>>(p, rho, u, nut, nt, rho0, vel, visc);
 }
-void launch_fields_q9(int st, const Params& p, int grid, double* rho, double* u, double* nut,
+void LBM_QNAME(launch_fields)(int st, const Params& p, int grid, double* rho, double* u, double* nut,
                        double* nt, double rho0, double vel, double visc, cudaStream_t s) {
   LBM_DISPATCH(fields_st, p, grid, rho, u, nut, nt, rho0, vel, visc, s)
 }
 
 template <int ST>
 static void reduce_st(const Params& p, int blocks, double* partial, long long chunk, cudaStream_t s) {
-  k_reduce<9, ST><<<blocks, RED_THREADS, 0, s>>>(p, partial, chunk);
+  k_reduce<LBM_Q, ST><<<blocks, RED_THREADS, 0, s>>>(p, partial, chunk);
 }
-void launch_reduce_q9(int st, const Params& p, int blocks, double* partial, long long chunk,
+void LBM_QNAME(launch_reduce)(int st, const Params& p, int blocks, double* partial, long long chunk,
                        cudaStream_t s) {
   LBM_DISPATCH(reduce_st, p, blocks, partial, chunk, s)
 }

@@ -34,6 +34,7 @@ struct lbm_ctx {
   double* utau_prev = nullptr;
   unsigned* flags = nullptr;
   unsigned last_flags = 0;
+  unsigned newton_count = 0;        // flags[1] at the last check
   double* partial = nullptr;       // FP64 reduction scratch: red_blocks * RED_VALS
   int red_blocks = 0;
   long long red_chunk = 0;
@@ -55,6 +56,7 @@ struct lbm_ctx {
 #define LBM_TMA_ZCHUNK 8
 #endif
   int tma_zchunk = LBM_TMA_ZCHUNK;     // z planes marched by one block
+  long long wait_limit = 1LL << 24;    // polls of a bounded device-side wait (Params::wait_limit)
   std::string err;
   std::vector<void*> allocs;
 };

@@ -18,6 +18,21 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+// Loads of the population and SA-field buffers.  The step kernels read buffers
+// that no thread of the same launch writes, so they mark their pointers
+// __restrict__ and read the records through the read-only path.  A persistent
+// kernel that advances several steps in one launch (the batch) reads data other
+// CTAs wrote earlier in the same launch: its translation unit defines
+// LBM_COHERENT_LOADS, which turns both off, so that every such load is a plain
+// global load ordered by the kernel's own fences.
+#ifdef LBM_COHERENT_LOADS
+#define LBM_RESTRICT
+#define LBM_LDG(p) (*(p))
+#else
+#define LBM_RESTRICT __restrict__
+#define LBM_LDG(p) __ldg(p)
+#endif
+
 namespace lbm {
 
 enum BcKind {
@@ -26,6 +41,8 @@ enum BcKind {
 };
 enum { XMIN = 0, XMAX = 1, YMIN = 2, YMAX = 3 };
 enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2, ST_FP64 = 3 };
+// flags[0]: failure bits; flags[1]: wall-node updates whose Newton iteration
+// reached its limit (count); flags[2..3] unused
 enum { FLAG_NONFINITE = 1u, FLAG_NEWTON = 2u, FLAG_TMA_TIMEOUT = 4u };
 // k_bulk row sets: ROWS_ALL every row; ROWS_INNER rows 1..ny-2 (independent of
 // the wall pre-pass, so they run concurrently with it) without the x-face
@@ -186,6 +203,7 @@ struct Params {
   void* frec[2];               // HRFD: rebuilt populations (Q per node), deviations, compute type
   const void* invd2;           // 1 / d^2 (wall distance of the SA model), compute type, [y][x]
   unsigned* flags;
+  long long wait_limit;        // polls of a bounded device-side wait before it gives up
 };
 
 // Parameter in the compute type: the float copy for FP32, the double for FP64.
@@ -194,19 +212,19 @@ template <> __device__ __forceinline__ float psel<float>(double, float f) { retu
 template <> __device__ __forceinline__ double psel<double>(double d, float) { return d; }
 
 // SA-field record of a cell: the velocity and nu_tilde, stored together (16 B
-// in FP32, 32 B in FP64).  ld_rec reads a record that no thread of the running
-// kernel writes (the source buffer) through the read-only path; st_rec writes
-// one with vector stores.
+// in FP32, 32 B in FP64).  ld_rec reads a record of the source buffer with one
+// vector load (through the read-only path unless LBM_COHERENT_LOADS); st_rec
+// writes one with vector stores.
 template <class R> struct Rec {
   R x, y, z, n;   // u_x, u_y, u_z, nu_tilde
 };
 template <class I> __device__ __forceinline__ Rec<float> ld_rec(const float* v, I id) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(v) + id);
+  const float4 a = LBM_LDG(reinterpret_cast<const float4*>(v) + id);
   return {a.x, a.y, a.z, a.w};
 }
 template <class I> __device__ __forceinline__ Rec<double> ld_rec(const double* v, I id) {
   const double2* q = reinterpret_cast<const double2*>(v) + 2 * id;
-  const double2 a = __ldg(q), b = __ldg(q + 1);
+  const double2 a = LBM_LDG(q), b = LBM_LDG(q + 1);
   return {a.x, a.y, b.x, b.y};
 }
 template <class I>
@@ -285,7 +303,7 @@ template <class R> struct Nb {
 };
 
 template <class R>
-__device__ __forceinline__ Nb<R> load_nb(const Params& p, const R* __restrict__ v, int x, int y,
+__device__ __forceinline__ Nb<R> load_nb(const Params& p, const R* LBM_RESTRICT v, int x, int y,
                                          int z) {
   const Rec<R> r = ld_rec(v, cidx(p, x, y, z));
   Nb<R> n;
@@ -297,7 +315,7 @@ __device__ __forceinline__ Nb<R> load_nb(const Params& p, const R* __restrict__ 
 }
 
 template <class R>
-__device__ Nb<R> neighbour(const Params& p, const R* __restrict__ v, int x, int y, int z,
+__device__ Nb<R> neighbour(const Params& p, const R* LBM_RESTRICT v, int x, int y, int z,
                            int axis, int s) {
   if (axis == 0) {
     int xn = x + s;
@@ -347,7 +365,7 @@ template <class R> __device__ __forceinline__ R inv_wall_dist2(const Params& p, 
 
 // Explicit Euler update of Eq. 11 at one cell, clipped at zero.
 template <class R, bool THREE_D>
-__device__ R sa_update(const Params& p, const R* __restrict__ v, int x, int y, int z) {
+__device__ R sa_update(const Params& p, const R* LBM_RESTRICT v, int x, int y, int z) {
   const Nb<R> c = load_nb<R>(p, v, x, y, z);
   const R nu = psel<R>(p.nu, p.nu_f);
   Nb<R> m[3], pl[3];
@@ -390,7 +408,7 @@ __device__ R sa_update(const Params& p, const R* __restrict__ v, int x, int y, i
 // record load per neighbour: x neighbours give nu_tilde, u_y, u_z; y
 // neighbours nu_tilde, u_x, u_z; z neighbours nu_tilde, u_x, u_y.
 template <class R, bool THREE_D>
-__device__ __forceinline__ R sa_update_interior(const Params& p, const R* __restrict__ v, int id,
+__device__ __forceinline__ R sa_update_interior(const Params& p, const R* LBM_RESTRICT v, int id,
                                                 int oxm, int oxp, int oym, int oyp, int ozm,
                                                 int ozp, int x, int y) {
   const R nu = psel<R>(p.nu, p.nu_f);
@@ -460,6 +478,42 @@ __host__ __device__ inline double wf_dudy(int law, double kap, double yp) {
   if (law == 1) return 1.0 / (kap * yp);
   const double ky = WF::kappa * yp, ky3 = ky * ky * ky, cv3 = WF::cv1 * WF::cv1 * WF::cv1;
   return (cv3 + ky3) / (cv3 + (1.0 + ky) * ky3);
+}
+
+// The same wall law and slope in FP32, for the wall-function values outside the
+// Newton inversion (u_B of Section 3.1, the slope of Eq. 15 in Eq. 27, the four
+// values of Eq. 29): a few ulp of FP32 (~1e-7 relative), where the FP64 forms
+// would run on GB300's FP64 pipe at 1/64 of the FP32 rate.
+__device__ __forceinline__ float wf_uplus_f(int law, float kap, float B, float yp) {
+  if (law == 1) return logf(yp) / kap + B;
+  const float s1 = yp + (float)WF::a1, s2 = yp + (float)WF::a2;
+  const float b1 = (float)WF::b1, b2 = (float)WF::b2;
+  return (float)WF::Bb + (float)WF::c1 * logf(s1 * s1 + b1 * b1) -
+         (float)WF::c2 * logf(s2 * s2 + b2 * b2) - (float)WF::c3 * atan2f(b1, s1) -
+         (float)WF::c4 * atan2f(b2, s2);
+}
+
+__device__ __forceinline__ float wf_dudy_f(int law, float kap, float yp) {
+  if (law == 1) return 1.0f / (kap * yp);
+  const float ky = (float)WF::kappa * yp, ky3 = ky * ky * ky;
+  const float cv3 = (float)(WF::cv1 * WF::cv1 * WF::cv1);
+  return (cv3 + ky3) / (cv3 + (1.0f + ky) * ky3);
+}
+
+// wall law and slope in the compute type (FP32 forms above, FP64 in the FP64 mode)
+template <class R> __device__ __forceinline__ R wf_uplus_r(const Params& p, R yp);
+template <> __device__ __forceinline__ float wf_uplus_r<float>(const Params& p, float yp) {
+  return wf_uplus_f(p.wall_law, (float)p.law_kappa, (float)p.law_B, yp);
+}
+template <> __device__ __forceinline__ double wf_uplus_r<double>(const Params& p, double yp) {
+  return wf_uplus(p.wall_law, p.law_kappa, p.law_B, yp);
+}
+template <class R> __device__ __forceinline__ R wf_dudy_r(const Params& p, R yp);
+template <> __device__ __forceinline__ float wf_dudy_r<float>(const Params& p, float yp) {
+  return wf_dudy_f(p.wall_law, (float)p.law_kappa, yp);
+}
+template <> __device__ __forceinline__ double wf_dudy_r<double>(const Params& p, double yp) {
+  return wf_dudy(p.wall_law, p.law_kappa, yp);
 }
 
 // Solve U = u u+(u y / nu) for u >= 0 (FP64).  Newton from the previous
@@ -548,7 +602,7 @@ __device__ typename Compute<ST>::R pull_bc(const Params& p, int x, int y, int z,
   using C = Codec<ST>;
   using R = typename Compute<ST>::R;
   using T = typename C::T;
-  const T* __restrict__ f = (const T*)p.f_src;
+  const T* LBM_RESTRICT f = (const T*)p.f_src;
   *known = true;
   const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
   int sx = x - cx;

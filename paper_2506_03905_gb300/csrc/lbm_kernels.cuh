@@ -50,9 +50,9 @@ __device__ __forceinline__ void interior_finish(const Params& p, const NbOff& o,
   using C = Codec<ST>;
   using R = typename Compute<ST>::R;
   using T = typename C::T;
-  T* __restrict__ fd = (T*)p.f_dst;
-  const R* __restrict__ vs = (const R*)p.v_src;
-  R* __restrict__ vd = (R*)p.v_dst;
+  T* LBM_RESTRICT fd = (T*)p.f_dst;
+  const R* LBM_RESTRICT vs = (const R*)p.v_src;
+  R* LBM_RESTRICT vd = (R*)p.v_dst;
   // SA working variable of the new step (Eq. 11)
   R ntn;
   if (p.turbulent)
@@ -78,7 +78,7 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
   using C = Codec<ST>;
   using R = typename Compute<ST>::R;
   using T = typename C::T;
-  const T* __restrict__ fs = (const T*)p.f_src;
+  const T* LBM_RESTRICT fs = (const T*)p.f_src;
   const NbOff o = nb_offsets(p, x, y, z);
   // pull streaming (Eq. 3): source x - c_i; issued first so that the loads are
   // in flight while the SA stencil is evaluated
@@ -125,9 +125,9 @@ __device__ __forceinline__ void bulk_wall_bb(const Params& p, int fi, int x, int
   using C = Codec<ST>;
   using R = typename Compute<ST>::R;
   using T = typename C::T;
-  const T* __restrict__ fs = (const T*)p.f_src;
-  T* __restrict__ fd = (T*)p.f_dst;
-  R* __restrict__ vd = (R*)p.v_dst;
+  const T* LBM_RESTRICT fs = (const T*)p.f_src;
+  T* LBM_RESTRICT fd = (T*)p.f_dst;
+  R* LBM_RESTRICT vd = (R*)p.v_dst;
   const NbOff o = nb_offsets(p, x, y, z);
   const int node = z * (p.nx - p.xw0[fi]) + (x - p.xw0[fi]);
   const R* uw = (const R*)p.uw[fi] + 3 * node;
@@ -196,9 +196,9 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
     }
   }
   const long long id = cidx(p, x, y, z);
-  T* __restrict__ fd = (T*)p.f_dst;
-  const R* __restrict__ vs = (const R*)p.v_src;
-  R* __restrict__ vd = (R*)p.v_dst;
+  T* LBM_RESTRICT fd = (T*)p.f_dst;
+  const R* LBM_RESTRICT vs = (const R*)p.v_src;
+  R* LBM_RESTRICT vd = (R*)p.v_dst;
 
   int wf = -1;
   if (y == 0 && p.wall[0] && x >= p.xw0[0]) wf = 0;
@@ -319,6 +319,11 @@ struct TmaTile {
   static_assert((XOFF * sizeof(T)) % 16 == 0 && (BW * sizeof(T)) % 16 == 0, "16-byte tiles");
 };
 
+// Polls of an mbarrier before a block of the TMA-staged kernel gives up on a
+// tile (the default of Params::wait_limit) and the bound of the drain that
+// follows a give-up.
+constexpr int kTmaDrainLimit = 1 << 24;
+
 // Minimum resident blocks per SM for the TMA-staged kernel (its register
 // budget); its two shared-memory stages take 2 x Q boxes per block.
 #ifndef LBM_TMA_MINB
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(256, LBM_TMA_MINB)
   const int z1 = min(p.nz, z0 + zchunk);
   const int x = x0 + tx, y = y0 + ty;
   const bool active = x < p.nx && y <= p.ny - 2;
-  const T* __restrict__ fs = (const T*)p.f_src;
+  const T* LBM_RESTRICT fs = (const T*)p.f_src;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -381,7 +386,7 @@ __global__ void __launch_bounds__(256, LBM_TMA_MINB)
       ++issued;
     }
     bool ok = false;
-    for (int it = 0; it < (1 << 24); ++it) {
+    for (long long it = 0; it < p.wait_limit; ++it) {
       if (mbar_try_wait(&bar[s], (uint32_t)((k >> 1) & 1))) {
         ok = true;
         break;
@@ -390,9 +395,12 @@ __global__ void __launch_bounds__(256, LBM_TMA_MINB)
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(p.flags, FLAG_TMA_TIMEOUT);
-        // the other stage may still have a copy in flight: wait for it (bounded)
+        // copies may still be in flight into this block's stages: wait for both
+        // (bounded by the default limit, whatever p.wait_limit is) before leaving
+        for (int it = 0; it < kTmaDrainLimit && !mbar_try_wait(&bar[s], (uint32_t)((k >> 1) & 1)); ++it) {
+        }
         if (issued > k + 1)
-          for (int it = 0; it < (1 << 24) && !mbar_try_wait(&bar[s ^ 1], (uint32_t)(((k + 1) >> 1) & 1)); ++it) {
+          for (int it = 0; it < kTmaDrainLimit && !mbar_try_wait(&bar[s ^ 1], (uint32_t)(((k + 1) >> 1) & 1)); ++it) {
           }
       }
       return;
@@ -446,34 +454,36 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
   const int x = p.xw0[fi] + node % nwx;
   const int yB = fi == 0 ? 0 : p.ny - 1;
   const int s = fi == 0 ? 1 : -1;   // inward direction along y
-  const R* __restrict__ vs = (const R*)p.v_src;
-  R* __restrict__ vd = (R*)p.v_dst;
-  const T* __restrict__ fs = (const T*)p.f_src;
+  const R* LBM_RESTRICT vs = (const R*)p.v_src;
+  R* LBM_RESTRICT vd = (R*)p.v_dst;
+  const T* LBM_RESTRICT fs = (const T*)p.f_src;
   const double nu = p.nu;
   const long long idB = cidx(p, x, yB, z);
   double ut = 0.0;
   bool ok = true;
 
   if (p.wall[fi] == BC_WALL_BB) {
-    // Section 3.2: u_tau from the tangential velocity at the reference node
+    // Section 3.2: u_tau from the tangential velocity at the reference node.
+    // Everything but the Newton inversion runs in the compute type R.
     const int yR = yB + s * (p.ref_node[fi] - 1);
     const double dw = p.d_w[fi];                       // y_B (1/2 half-way)
     const double yref = (double)(p.ref_node[fi] - 1) + dw;
     const long long idR = cidx(p, x, yR, z);
-    const double Ux = (double)vs[4 * idR], Uz = (double)vs[4 * idR + 2];
-    const double U = sqrt(Ux * Ux + Uz * Uz);
-    const double tx = U > 0.0 ? Ux / U : 1.0, tz = U > 0.0 ? Uz / U : 0.0;
+    const R Ux = vs[4 * idR], Uz = vs[4 * idR + 2];
+    const R Um = nn_sqrt(Ux * Ux + Uz * Uz);
+    const R iU = Um > (R)0 ? (R)1 / Um : (R)0;
+    const R tx = Um > (R)0 ? Ux * iU : (R)1, tz = Uz * iU;
     R* uw = (R*)p.uw[fi] + 3 * node;
     if (p.turbulent) {
-      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, U, yref, nu, p.utau[fi][node], &ut);
-      const double ypB = ut * dw / nu;
-      const double nutB = nu * WF::kappa * ypB;
+      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, (double)Um, yref, nu, p.utau[fi][node], &ut);
+      const R utr = (R)ut, nur = psel<R>(p.nu, p.nu_f), kap = (R)WF::kappa;
+      const R ypB = utr * (R)dw * psel<R>(p.inv_nu, p.inv_nu_f);
       // Eq. 35 with Delta_w = y_B = d_w and nu_t|_B = nu kappa y_B+
-      const double slip = ut * ut * dw / (nu + nutB);
-      uw[0] = (R)((double)vs[4 * idB] - slip * tx);
+      const R slip = fdiv(utr * utr * (R)dw, nur * ((R)1 + kap * ypB));
+      uw[0] = vs[4 * idB] - slip * tx;
       uw[1] = (R)0;
-      uw[2] = (R)((double)vs[4 * idB + 2] - slip * tz);
-      vd[4 * idB + 3] = (R)(nu * WF::kappa * ypB);
+      uw[2] = vs[4 * idB + 2] - slip * tz;
+      vd[4 * idB + 3] = nur * kap * ypB;
     } else {
       uw[0] = uw[1] = uw[2] = (R)0;
     }
@@ -495,15 +505,20 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
       jF[1] += (R)L::c(i, 1) * gi;
       jF[2] += (R)L::c(i, 2) * gi;
     }
-    const double Ux = ((double)jF[0] + p.Ush) / (double)rhoF, Uz = (double)(jF[2] / rhoF);
-    const double U = sqrt(Ux * Ux + Uz * Uz);
-    const double tx = U > 0.0 ? Ux / U : 1.0, tz = U > 0.0 ? Uz / U : 0.0;
+    // everything but the Newton inversion runs in the compute type R
+    const R irF = fdiv((R)1, rhoF);
+    const R Ux = (jF[0] + psel<R>(p.Ush, p.Ush_f)) * irF, Uz = jF[2] * irF;
+    const R Um = nn_sqrt(Ux * Ux + Uz * Uz);
+    const R iU = Um > (R)0 ? (R)1 / Um : (R)0;
+    const R tx = Um > (R)0 ? Ux * iU : (R)1, tz = Uz * iU;
     const double dw = p.d_w[fi];                       // y_B; y_F = 1 + d_w
     if (p.turbulent)
-      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, U, 1.0 + dw, nu, p.utau[fi][node], &ut);
-    const double ypB = ut * dw / nu;
-    const double upB = p.turbulent ? ut * wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB) : 0.0;
-    const R uB[3] = {(R)(upB * tx), (R)0, (R)(upB * tz)};
+      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, (double)Um, 1.0 + dw, nu, p.utau[fi][node],
+                      &ut);
+    const R utr = (R)ut, inu = psel<R>(p.inv_nu, p.inv_nu_f);
+    const R ypB = utr * (R)dw * inu;
+    const R upB = p.turbulent ? utr * wf_uplus_r<R>(p, ypB) : (R)0;   // u_B = u_tau u+(y_B+)
+    const R uB[3] = {upB * tx, (R)0, upB * tz};
     // Eq. 23 with u_B . n = 0: rho_B = f_par + 2 f_perp (deviations: weights sum to 1)
     R gpar = 0, gperp = 0;
 #pragma unroll
@@ -532,40 +547,39 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     }
     const long long idF = cidx(p, x, yF, z), idFF = cidx(p, x, yFF, z);
     const bool cai = p.wall[fi] == BC_WALL_CAI;
-    double ana;
+    R ana;
     if (cai) {
       // Eq. 29: (u_tau / Delta)(-11/6 u+(y_B+) + 3 u+(y_B+ + D+) - 3/2 u+(y_B+ + 2D+)
       //          + 1/3 u+(y_B+ + 3D+)), Delta = 1, D+ = u_tau / nu
-      const double dp = ut / nu;
-      ana = ut > 0.0
-                ? ut * (-11.0 / 6.0 * wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB) +
-                        3.0 * wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB + dp) -
-                        1.5 * wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB + 2.0 * dp) +
-                        wf_uplus(p.wall_law, p.law_kappa, p.law_B, ypB + 3.0 * dp) / 3.0)
-                : 0.0;
+      const R dp = utr * inu;
+      ana = ut > 0.0 ? utr * ((R)(-11.0 / 6.0) * wf_uplus_r<R>(p, ypB) +
+                              (R)3 * wf_uplus_r<R>(p, ypB + dp) -
+                              (R)1.5 * wf_uplus_r<R>(p, ypB + (R)2 * dp) +
+                              wf_uplus_r<R>(p, ypB + (R)3 * dp) * (R)(1.0 / 3.0))
+                     : (R)0;
     } else {
-      const double dup = ypB > 0.0 ? wf_dudy(p.wall_law, p.law_kappa, ypB) : 1.0;
-      ana = ut > 0.0 ? ut * ut / nu * dup : 0.0;   // Eq. 15
+      const R dup = ypB > (R)0 ? wf_dudy_r<R>(p, ypB) : (R)1;
+      ana = ut > 0.0 ? utr * utr * inu * dup : (R)0;   // Eq. 15
     }
-    const double tdir[3] = {tx, 0.0, tz};
+    const R tdir[3] = {tx, (R)0, tz};
     const R beta = cai ? (R)1 : (R)p.beta[fi];     // Eq. 30: beta = 1 with Eq. 29
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const R fd = (R)0.5 * ((R)-3 * vs[4 * idB + c] + (R)4 * vs[4 * idF + c] -
                              vs[4 * idFF + c]);                              // Eq. 28
       R dn = fd;
-      if (c != 1 && p.turbulent) dn = beta * (R)(ana * tdir[c]) + ((R)1 - beta) * fd;  // Eq. 27
+      if (c != 1 && p.turbulent) dn = beta * (ana * tdir[c]) + ((R)1 - beta) * fd;  // Eq. 27
       G[1][c] = (R)s * dn;
     }
     const R ntB = vs[4 * idB + 3];
     const R nutB = p.turbulent ? sa_nut<R>(ntB, psel<R>(p.inv_nu, p.inv_nu_f)) : (R)0;
-    const R tau = (R)0.5 + (R)3 * ((R)nu + nutB);
+    const R tau = (R)0.5 + (R)3 * (psel<R>(p.nu, p.nu_f) + nutB);
     const R Sxx = G[0][0], Syy = G[1][1], Szz = G[2][2];
     const R Sxy = (R)0.5 * (G[0][1] + G[1][0]), Sxz = (R)0.5 * (G[0][2] + G[2][0]),
             Syz = (R)0.5 * (G[1][2] + G[2][1]);
-    const R trS = (Sxx + Syy + Szz) / (R)3;
+    const R trS = (Sxx + Syy + Szz) * (R)(1.0 / 3.0);
     const R Us = psel<R>(p.Ush, p.Ush_f);
-    const R dux = (R)(upB * tx - p.Ush);
+    const R dux = uB[0] - Us;
     const R uu15 = (R)1.5 * (uB[0] * uB[0] + uB[2] * uB[2]);
     const R du15 = (R)1.5 * (dux * ((R)2 * Us + dux) + uB[2] * uB[2]);
     R* fr = (R*)p.frec[fi] + (long long)node * Q;
@@ -577,10 +591,13 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
                    (R)2 * ((R)(cx * cy) * Sxy + (R)(cx * cz) * Sxz + (R)(cy * cz) * Syz) - trS;
       fr[i] = geq - (R)3 * (R)L::w(i) * rhoB * tau * qs;     // Eqs. 19, 26
     }
-    if (p.turbulent) vd[4 * idB + 3] = (R)(nu * WF::kappa * ypB);
+    if (p.turbulent) vd[4 * idB + 3] = psel<R>(p.nu, p.nu_f) * (R)WF::kappa * ypB;
   }
   p.utau[fi][node] = ut;
-  if (!ok) atomicOr(p.flags, FLAG_NEWTON);
+  if (!ok) {   // Newton reached its iteration limit: flag and count the node update
+    atomicOr(p.flags, FLAG_NEWTON);
+    atomicAdd(p.flags + 1, 1u);
+  }
 }
 
 template <int Q, int ST>

@@ -12,7 +12,10 @@
 // The scratch array below is loaded with the library on every GPU that loads
 // it and stays there until the process exits.  Its address is looked up once
 // per device, on that device's first call (so the first call on a device
-// should come before any stream capture).  All calls share it: two calls
+// should come before any stream capture), and kept for the life of the
+// process: after a cudaDeviceReset the module is loaded again and the kept
+// address is stale, so this entry point must not be used on a device after it
+// has been reset.  All calls share it: two calls
 // whose kernels overlap on the GPU (different streams, or different host
 // threads on one device) race on it and must be serialised by the caller.
 // Each call writes every partial sum it later reads, so nothing has to be
@@ -138,9 +141,13 @@ extern "C" lbm_status lbm_moments_noalloc(const void* f, int lattice, int storag
                                 std::to_string(max_cells) + " cells");
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+  if (e != cudaSuccess)
     return fail(LBM_ECUDA, std::string("lbm_moments_noalloc: no usable current device: ") +
                                cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(LBM_EUNSUPPORTED, "lbm_moments_noalloc: device index " + std::to_string(dev) +
+                                      " is beyond the " + std::to_string(kMaxDevices) +
+                                      " devices this entry point keeps an address for");
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -158,6 +165,12 @@ extern "C" lbm_status lbm_moments_noalloc(const void* f, int lattice, int storag
   }
   const int blocks = (int)((n + kNoAllocCellsPerBlock - 1) / kNoAllocCellsPerBlock);
   cudaStream_t s = (cudaStream_t)stream;
+  // an error left pending by an earlier, unrelated call is reported as such, so
+  // that the check after the launches sees only this call's launch errors
+  e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(LBM_ECUDA, std::string("lbm_moments_noalloc: a CUDA error was pending before "
+                                       "this call: ") + cudaGetErrorString(e));
   if (lattice == LBM_D2Q9) launch_partial<9>(storage, f, nx, ny, nz, pitch, scratch, blocks, s);
   else launch_partial<19>(storage, f, nx, ny, nz, pitch, scratch, blocks, s);
   k_moments_final<<<1, 32, 0, s>>>(scratch, blocks, out);

@@ -29,14 +29,21 @@ def _state_populations(solver, case):
     return torch.from_numpy(raw).cuda(), q, pitch
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16"])
-def test_noalloc_moments_match_diagnostics_twice(storage):
+# nx = 37 is not a multiple of 8, so rows are padded (pitch 40 > nx); 17,760
+# cells take five blocks of the reduction, the last one partial
+SIZES = {"D2Q9": (37, 480, 1), "D3Q19": (37, 24, 20)}
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16", "fp64"])
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_noalloc_moments_match_diagnostics_twice(lattice, storage):
     import torch
     import paper_2506_03905_gb300 as pkg
+    nx, ny, nz = SIZES[lattice]
     # populations stored as f_i - w_i (no reference-velocity shift), the layout
     # the entry point documents
-    case = C.channel_3d(re_tau=5200.0, scheme="wall_bb", nx=40, ny=20, nz=5, seed=3,
-                        storage=storage).replace(u_shift=0.0)
+    case = C.channel_3d(re_tau=5200.0, scheme="wall_bb", nx=nx, ny=ny, nz=nz, seed=3,
+                        storage=storage).replace(u_shift=0.0, lattice=lattice)
     s = pkg.Solver(case)
     s.set_fields(*C.initial_fields(case))
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
@@ -45,6 +52,7 @@ def test_noalloc_moments_match_diagnostics_twice(storage):
         s.step(nsteps)
         d = s.diagnostics()
         f, q, pitch = _state_populations(s, case)
+        assert pitch > nx
         out.fill_(-1.0)
         st = pkg.lbm_moments_noalloc(f.data_ptr(), q, pkg.STORAGE[storage], case.nx, case.ny,
                                      case.nz, pitch, out.data_ptr(), stream)
