@@ -156,6 +156,13 @@ def dean_bulk_reynolds(re_tau: float) -> float:
     return (8.0 / 0.073) ** (4.0 / 7.0) * re_tau ** (8.0 / 7.0)
 
 
+def dean_cfb(re_b: float) -> float:
+    """Dean's correlation in friction-coefficient form, C_fb = 0.073 Re_b^(-1/4): with
+    C_fb = 2 (u_tau / U_b)^2 = 8 (Re_tau / Re_b)^2 it is the Re_b(Re_tau) relation of
+    Section 4.1.1."""
+    return 0.073 * re_b ** -0.25
+
+
 def channel_parameters(re_tau: float, h: float = 1.0, nu: float = NU_AIR):
     """u_tau, g, Re_b, U_b, C_fb, y(y+=50) of Table 2 for a given Re_tau."""
     u_tau = re_tau * nu / h
@@ -182,6 +189,18 @@ def half_channel_2d(re_tau: float = 2000.0, ny: int = 48, nx: int = 4,
         collision="bgk", storage=storage, turbulence="sa", wall_law="log",
         bcs={"ymin": BC("wall_bb", ref_node=1), "ymax": BC("symmetry")},
         u_init=(0.0, 0.0, 0.0), nut_ratio_init=3.0, steps=steps)
+
+
+def channel_reynolds_sweep(re_tau: float, scheme: str = "wall_hrfd", n: int = 20,
+                           storage: str = "fp64") -> Case:
+    """2-D half channel of the Reynolds-number study (Section 4.1.2.6): D2Q9, N = 20
+    cells from the wall to the symmetric centreline, periodic in x (4 cells),
+    SA model with the SA-consistent wall function (Eq. 16) and the reference
+    node F, BGK, initial u = U_b from Dean's correlation, nu_tilde = 3 nu."""
+    c = half_channel_2d(re_tau=re_tau, ny=n, nx=4, storage=storage)
+    p = channel_parameters(re_tau)
+    return c.replace(name=f"channel_re_sweep_Re{int(re_tau)}_{scheme}_N{n}", wall_law="sa_analytic",
+                     bcs={"ymin": BC(scheme, ref_node=2)}, u_init=(p["u_b"], 0.0, 0.0))
 
 
 def channel_3d(re_tau: float = 5200.0, scheme: str = "wall_bb", nx: int = 256,

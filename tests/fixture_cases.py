@@ -62,6 +62,19 @@ CASES = {
 }
 
 
+# Reynolds-number study of Section 4.1.2.6 (Fig. 12): converged runs, stopped by
+# the criterion of Section 4.1.1 applied per chunk of CFB_CHECK steps
+CFB_RE_TAU = (2000.0, 4200.0, 8000.0, 20000.0)
+CFB_SCHEMES = ("wall_hrfd", "wall_bb", "wall_cai_degrigny")
+CFB_TOL, CFB_CHECK, CFB_MAX = 1e-4, 1000, 200000
+CFB_CASES = {f"cfb_Re{int(r)}_{s}": (r, s) for r in CFB_RE_TAU for s in CFB_SCHEMES}
+
+
+def cfb_case(name):
+    r, s = CFB_CASES[name]
+    return C.channel_reynolds_sweep(r, s)
+
+
 def case_signature(case) -> str:
     """Every parameter of the case except its storage type (the oracle is FP64)."""
     d = dataclasses.asdict(case)
@@ -114,6 +127,19 @@ def reduce_fields(case, fields):
 
 def path(name):
     return os.path.join(FIXDIR, name + ".npz")
+
+
+def load_cfb(name):
+    """(case, results) of a stored Reynolds-study fixture."""
+    case = cfb_case(name)
+    p = path(name)
+    if not os.path.exists(p):
+        raise FileNotFoundError(f"{p} missing: run tests/golden/make_oracle_fixtures.py {name}")
+    with np.load(p, allow_pickle=False) as z:
+        meta = json.loads(str(z["meta"]))
+    if meta["signature"] != case_signature(case):
+        raise RuntimeError(f"{p} was made from another case definition: regenerate it")
+    return case, meta
 
 
 def load(name):

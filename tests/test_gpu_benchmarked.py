@@ -255,3 +255,37 @@ def test_fp16_batch_matches_single_fp16_instances():
         c = cases[i]
         r = Oracle(c, *C.initial_fields(c)).run(nsteps).fields()
         assert _cf_err(c, got[i], r) <= 1e-2, (c.name, _cf_err(c, got[i], r))
+
+
+# ------------------------------------------ Reynolds-number study (Fig. 12)
+
+@pytest.mark.parametrize("name", sorted(FX.CFB_CASES))
+def test_converged_bulk_friction_matches_oracle(name):
+    """Converged 2-D half channels of Section 4.1.2.6 (N = 20, Re_tau 2e3 - 2e4,
+    three wall schemes).  FP64 storage through lbm_run_to_convergence: the run
+    stops at the oracle's chunk and C_fb = 2 (u_tau / U_b)^2 and U_b match the
+    oracle's to 1e-9.  FP32 storage over the same number of steps: 1e-5."""
+    import paper_2506_03905_gb300 as pkg
+    case, ref = FX.load_cfb(name)
+
+    def bulk(s):
+        f = s.fields(["u", "u_tau_ymin"])
+        u_b, u_tau = float(f["u"][0].mean()), float(f["u_tau_ymin"].mean())
+        return u_b, 2.0 * (u_tau / u_b) ** 2
+
+    s = pkg.Solver(case.replace(storage="fp64"))
+    s.set_fields(*C.initial_fields(case))
+    steps, res = s.run_to_convergence(FX.CFB_TOL, FX.CFB_CHECK, FX.CFB_MAX)
+    u_b, cfb = bulk(s)
+    s.close()
+    assert steps == ref["steps"], (steps, ref["steps"], res, ref["residual"])
+    assert res < FX.CFB_TOL
+    assert abs(cfb - ref["cfb"]) <= 1e-9 * ref["cfb"], (cfb, ref["cfb"])
+    assert abs(u_b - ref["u_b"]) <= 1e-9 * ref["u_b"], (u_b, ref["u_b"])
+    s = pkg.Solver(case.replace(storage="fp32"))
+    s.set_fields(*C.initial_fields(case))
+    s.step(ref["steps"])
+    u_b, cfb = bulk(s)
+    s.close()
+    assert abs(cfb - ref["cfb"]) <= 1e-5 * ref["cfb"], (cfb, ref["cfb"])
+    assert abs(u_b - ref["u_b"]) <= 1e-5 * ref["u_b"], (u_b, ref["u_b"])
