@@ -3,10 +3,14 @@
 //
 // Work is split into items, each taken by one warp: chunks of 32 wall nodes
 // of one y face of one instance (the wall pre-pass, kind A), ranges of cells
-// of the rows without wall nodes of one instance (kind B), and ranges of cells
-// of the wall rows of one instance (kind W, which read what the instance's A
-// items of the same step wrote).  The items of one step are listed as
-//   A items of every instance, then for each instance its B and W items,
+// of the rows without wall nodes of one instance (kind B, or kind I when all
+// of them have in-lattice or periodic neighbours and take the face-free path),
+// and ranges of cells of the wall rows of one instance (kind W, which read what
+// the instance's A items of the same step wrote).  The D3Q19 and the D2Q9
+// instances form two groups, each advanced by its own kernel (one velocity set
+// per kernel keeps the code a warp may jump to small); the two launches run one
+// after the other.  The items of one step of a group are listed as
+//   A items of every instance, then for each instance its B / I and W items,
 // and the steps of a launch follow one another.  Warps take items in that
 // order from one atomic ticket counter, so every item a warp may wait on has an
 // earlier ticket and is held by a running warp: no deadlock, and no grid-wide
@@ -54,18 +58,21 @@ struct BatchInst {
   int itemsA;    // wall pre-pass items of one step
 };
 
-enum { KIND_A = 0, KIND_B = 1, KIND_W = 2 };
+// KIND_I: cells of rows without wall nodes whose six neighbours are all in the
+// lattice or periodic (a channel instance's rows 1..ny-2): the face-free path
+enum { KIND_A = 0, KIND_B = 1, KIND_W = 2, KIND_I = 3 };
 
 struct WorkItem {
   int inst;
-  int kind;      // KIND_A / KIND_B / KIND_W
+  int kind;      // KIND_A / KIND_B / KIND_I / KIND_W
   int face;      // KIND_A: 0 = ymin, 1 = ymax
   int begin, end;   // wall nodes (A) or cells of the item's row set (B, W)
   int pad[2];
 };
 
-// Control block of one launch, cleared before it: the ticket counter, the
-// failure flag, then per instance the finished items and finished A items.
+// Control block of one launch of a lattice group, cleared before it: the ticket
+// counter and the failure flag.  The per-instance counts of finished items and
+// finished A items follow the two groups' blocks.
 struct BatchCtl {
   unsigned long long next;
   unsigned err;
@@ -137,7 +144,7 @@ __device__ __forceinline__ void warp_load_params(Params* dst, const Params* src,
 __device__ __forceinline__ void item_cell(const Params& p, int kind, bool walls, int c, int* x,
                                           int* y, int* z) {
   const int nx = p.nx;
-  const int nrow = kind == KIND_W ? 2 : (walls ? p.ny - 2 : p.ny);
+  const int nrow = kind == KIND_W ? 2 : (walls ? p.ny - 2 : p.ny);   // KIND_B / KIND_I
   const int per_z = nx * nrow;
   *z = c / per_z;
   const int r = c - *z * per_z;
@@ -146,7 +153,10 @@ __device__ __forceinline__ void item_cell(const Params& p, int kind, bool walls,
   *y = kind == KIND_W ? (j == 0 ? 0 : p.ny - 1) : (walls ? j + 1 : j);
 }
 
-template <int ST>
+// One kernel per lattice: the code a warp may run holds one velocity set only
+// (instruction-fetch stalls dominated a kernel holding both), and the two
+// launches of a batch step one after the other, each over its own instances.
+template <int ST, int Q>
 __global__ void LBM_BATCH_BOUNDS k_batch(BatchInst* inst, const WorkItem* items, int nitems,
                                          BatchCtl* ctl, unsigned* done, unsigned* done_a,
                                          int nsteps, long long spin_limit) {
@@ -173,19 +183,15 @@ __global__ void LBM_BATCH_BOUNDS k_batch(BatchInst* inst, const WorkItem* items,
     if (!ok) break;
     warp_load_params(&sp[wib], &b.p[(b.cur + step) & 1], lane);
     const Params& p = sp[wib];
-    const int Q = b.Q;
     if (w.kind == KIND_A) {
-      for (int node = w.begin + lane; node < w.end; node += 32) {
-        if (Q == 19) wall_node<19, ST>(p, w.face, node);
-        else wall_node<9, ST>(p, w.face, node);
-      }
+      for (int node = w.begin + lane; node < w.end; node += 32) wall_node<Q, ST>(p, w.face, node);
     } else {
       const bool walls = per_a > 0;
       for (int c = w.begin + lane; c < w.end; c += 32) {
         int x, y, z;
         item_cell(p, w.kind, walls, c, &x, &y, &z);
-        if (Q == 19) bulk_cell<19, ST, true>(p, x, y, z);
-        else bulk_cell<9, ST, true>(p, x, y, z);
+        if (w.kind == KIND_I) bulk_interior<Q, ST>(p, x, y, z);
+        else bulk_cell<Q, ST, true>(p, x, y, z);
       }
     }
     __syncwarp();
@@ -202,14 +208,15 @@ __global__ void LBM_BATCH_BOUNDS k_batch(BatchInst* inst, const WorkItem* items,
 using BatchKernel = void (*)(BatchInst*, const WorkItem*, int, BatchCtl*, unsigned*, unsigned*, int,
                              long long);
 
-BatchKernel batch_kernel(int st) {
+template <int Q> BatchKernel batch_kernel_q(int st) {
   switch (st) {
-    case ST_FP32: return k_batch<ST_FP32>;
-    case ST_FP16: return k_batch<ST_FP16>;
-    case ST_BF16: return k_batch<ST_BF16>;
-    default: return k_batch<ST_FP64>;
+    case ST_FP32: return k_batch<ST_FP32, Q>;
+    case ST_FP16: return k_batch<ST_FP16, Q>;
+    case ST_BF16: return k_batch<ST_BF16, Q>;
+    default: return k_batch<ST_FP64, Q>;
   }
 }
+BatchKernel batch_kernel(int st, int q) { return q == 19 ? batch_kernel_q<19>(st) : batch_kernel_q<9>(st); }
 
 std::string g_batch_err;
 
@@ -221,20 +228,23 @@ struct lbm_batch {
   cudaStream_t stream = nullptr;
   BatchInst* d_inst = nullptr;
   std::vector<BatchInst> h_inst;
+  // lattice groups: 0 = D3Q19 instances, 1 = D2Q9 instances, each advanced by
+  // its own kernel; the items of group g are d_items[item_off[g] ...]
   WorkItem* d_items = nullptr;
-  int nitems = 0;                // items of one step
-  void* d_ctl = nullptr;         // BatchCtl, then done[n], done_a[n]
+  int nitems[2] = {0, 0};        // items of one step per group
+  int item_off[2] = {0, 0};
+  void* d_ctl = nullptr;         // BatchCtl per group, then done[n], done_a[n]
   size_t ctl_bytes = 0;
   int threads = 256;
-  int tile = 256;                // cells per B / W item (one warp each)
-  int grid = 0;
+  int tile = 256;                // cells per B / I / W item (one warp each)
+  int grid[2] = {0, 0};
   bool tuned = false;
   bool use_graph = true;         // false if capturing the cooperative launch was refused
   cudaGraphExec_t gexec = nullptr;
   int g_nsteps = -1;
   std::vector<int> dev_cur;      // buffer parity of each instance as the device holds it
   long long spin_limit = kSpinLimit;   // polls before a warp gives up at a wait
-  BatchCtl* h_ctl = nullptr;     // pinned copy of the control block after each launch
+  BatchCtl* h_ctl = nullptr;     // pinned copy of the groups' control blocks after each launch
   cudaEvent_t ev_ctl = nullptr;
   bool ctl_pending = false;      // a launch's control copy has not been inspected yet
   std::string err;
@@ -256,23 +266,17 @@ static void drop_graph(lbm_batch* b) {
   }
 }
 
-// Instances in work-item order: D3Q19 first, then D2Q9, so that the warps of
-// an SM mostly run one lattice's code at a time (instruction-cache locality).
-static std::vector<int> instance_order(const lbm_batch* b) {
-  std::vector<int> order;
-  for (int q : {19, 9})
-    for (int i = 0; i < (int)b->ctxs.size(); ++i)
-      if (b->ctxs[i]->Q == q) order.push_back(i);
-  return order;
-}
+static int group_q(int g) { return g == 0 ? 19 : 9; }
 
-// The items of one step: wall-node chunks of 32 of every instance first, then
-// per instance its ranges of `tile` cells of the rows without wall nodes and of
-// the wall rows.
-static lbm_status build_items(lbm_batch* b, int tile) {
-  std::vector<WorkItem> items;
-  const std::vector<int> order = instance_order(b);
-  std::vector<int> per(b->ctxs.size(), 0), per_a(b->ctxs.size(), 0);
+// The items of one step of a lattice group: wall-node chunks of 32 of every
+// instance first, then per instance its ranges of `tile` cells of the rows
+// without wall nodes (face-free when the instance is periodic along x and those
+// rows have in-lattice neighbours along y) and of the wall rows.
+static void group_items(const lbm_batch* b, int g, int tile, std::vector<WorkItem>& items,
+                        std::vector<int>& per_a) {
+  std::vector<int> order;
+  for (int i = 0; i < (int)b->ctxs.size(); ++i)
+    if (b->ctxs[i]->Q == group_q(g)) order.push_back(i);
   for (int i : order) {
     const lbm_ctx* c = b->ctxs[i];
     for (int f = 0; f < 2; ++f) {
@@ -287,18 +291,29 @@ static lbm_status build_items(lbm_batch* b, int tile) {
   for (int i : order) {
     const lbm_ctx* c = b->ctxs[i];
     const bool walls = per_a[i] > 0;
+    const bool face_free = c->base.px && (walls ? c->ny >= 3 : c->base.py);
+    const int kind = face_free ? KIND_I : KIND_B;
     const int nb = c->nx * c->nz * (walls ? c->ny - 2 : c->ny);
-    for (int a = 0; a < nb; a += tile) items.push_back({i, KIND_B, 0, a, std::min(nb, a + tile), {0, 0}});
+    for (int a = 0; a < nb; a += tile) items.push_back({i, kind, 0, a, std::min(nb, a + tile), {0, 0}});
     if (walls) {
       const int nwr = 2 * c->nx * c->nz;
       for (int a = 0; a < nwr; a += tile)
         items.push_back({i, KIND_W, 0, a, std::min(nwr, a + tile), {0, 0}});
     }
   }
+}
+
+static lbm_status build_items(lbm_batch* b, int tile) {
+  std::vector<WorkItem> items;
+  std::vector<int> per(b->ctxs.size(), 0), per_a(b->ctxs.size(), 0);
+  for (int g = 0; g < 2; ++g) {
+    b->item_off[g] = (int)items.size();
+    group_items(b, g, tile, items, per_a);
+    b->nitems[g] = (int)items.size() - b->item_off[g];
+  }
   for (const WorkItem& w : items) ++per[w.inst];
   if (b->d_items) cudaFree(b->d_items);
   b->d_items = nullptr;
-  b->nitems = (int)items.size();
   BATCH_TRY(b, cudaMalloc(&b->d_items, std::max<size_t>(1, items.size()) * sizeof(WorkItem)));
   BATCH_TRY(b, cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem),
                           cudaMemcpyHostToDevice));
@@ -322,47 +337,56 @@ static lbm_status build_items(lbm_batch* b, int tile) {
 }
 
 static lbm_status set_threads(lbm_batch* b, int threads) {
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0;
   BATCH_TRY(b, cudaGetDevice(&dev));
   BATCH_TRY(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  BATCH_TRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->st), threads, 0));
-  if (per_sm < 1) {
-    b->err = "the batch kernel does not fit on an SM with this block size";
-    return LBM_EUNSUPPORTED;
+  for (int g = 0; g < 2; ++g) {
+    int per_sm = 0;
+    BATCH_TRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->st, group_q(g)),
+                                                               threads, 0));
+    if (per_sm < 1) {
+      b->err = "the batch kernel does not fit on an SM with this block size";
+      return LBM_EUNSUPPORTED;
+    }
+    b->grid[g] = sms * per_sm;
   }
   b->threads = threads;
-  b->grid = sms * per_sm;
   drop_graph(b);
   return LBM_OK;
 }
 
 // Enqueue the control-block reset and one cooperative launch advancing every
 // instance by nsteps.
+// Enqueue the control-block reset and, per lattice group with instances, one
+// cooperative launch advancing them by nsteps (the groups one after the other).
 static lbm_status launch(lbm_batch* b, int nsteps, cudaStream_t s) {
   BATCH_TRY(b, cudaMemsetAsync(b->d_ctl, 0, b->ctl_bytes, s));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(b->grid, 1, 1);
-  cfg.blockDim = dim3(b->threads, 1, 1);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
   BatchCtl* ctl = (BatchCtl*)b->d_ctl;
-  unsigned* done = (unsigned*)((char*)b->d_ctl + sizeof(BatchCtl));
+  unsigned* done = (unsigned*)((char*)b->d_ctl + 2 * sizeof(BatchCtl));
   unsigned* done_a = done + b->ctxs.size();
-  BATCH_TRY(b, cudaLaunchKernelEx(&cfg, batch_kernel(b->st), b->d_inst,
-                                  (const WorkItem*)b->d_items, b->nitems, ctl, done, done_a, nsteps,
-                                  b->spin_limit));
+  for (int g = 0; g < 2; ++g) {
+    if (b->nitems[g] == 0) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->grid[g], 1, 1);
+    cfg.blockDim = dim3(b->threads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BATCH_TRY(b, cudaLaunchKernelEx(&cfg, batch_kernel(b->st, group_q(g)), b->d_inst,
+                                    (const WorkItem*)b->d_items + b->item_off[g], b->nitems[g],
+                                    ctl + g, done, done_a, nsteps, b->spin_limit));
+  }
   return LBM_OK;
 }
 
 // After a launch on b->stream: copy the control block to pinned host memory
 // behind it, to be inspected later without blocking the host.
 static lbm_status queue_ctl_copy(lbm_batch* b) {
-  BATCH_TRY(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost,
+  BATCH_TRY(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, 2 * sizeof(BatchCtl), cudaMemcpyDeviceToHost,
                                b->stream));
   BATCH_TRY(b, cudaEventRecord(b->ev_ctl, b->stream));
   b->ctl_pending = true;
@@ -383,8 +407,8 @@ static lbm_status poll_ctl(lbm_batch* b, bool blocking) {
     BATCH_TRY(b, q);
   }
   b->ctl_pending = false;
-  if (b->h_ctl->err) {
-    b->h_ctl->err = 0;
+  if (b->h_ctl[0].err || b->h_ctl[1].err) {
+    b->h_ctl[0].err = b->h_ctl[1].err = 0;
     for (int& d : b->dev_cur) d = -1;
     b->err = "a bounded wait of the batch kernel gave up; the instances' states are not valid";
     return LBM_ETIMEOUT;
@@ -469,16 +493,16 @@ extern "C" lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** 
     b->h_inst[i].Q = c->Q;
     b->h_inst[i].cur = c->cur;
   }
-  b->ctl_bytes = sizeof(BatchCtl) + 2 * (size_t)n * sizeof(unsigned);
+  b->ctl_bytes = 2 * sizeof(BatchCtl) + 2 * (size_t)n * sizeof(unsigned);
   if (cudaMalloc(&b->d_inst, n * sizeof(BatchInst)) != cudaSuccess ||
       cudaMalloc(&b->d_ctl, b->ctl_bytes) != cudaSuccess ||
-      cudaMallocHost(&b->h_ctl, sizeof(BatchCtl)) != cudaSuccess ||
+      cudaMallocHost(&b->h_ctl, 2 * sizeof(BatchCtl)) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_ctl, cudaEventDisableTiming) != cudaSuccess) {
     g_batch_err = "lbm_batch_create: device allocation failed";
     lbm_batch_destroy(b);
     return LBM_ENOMEM;
   }
-  std::memset(b->h_ctl, 0, sizeof(BatchCtl));
+  std::memset(b->h_ctl, 0, 2 * sizeof(BatchCtl));
   // the contexts' pending work (state set-up) must be complete before the batch
   // reads their parameters on another order of launches
   for (lbm_ctx* c : b->ctxs) cudaStreamSynchronize(c->stream);
@@ -615,7 +639,7 @@ extern "C" lbm_status lbm_batch_info(const lbm_batch* b, int out[4]) {
   out[0] = b->threads;
   out[1] = b->tile;
   out[2] = b->use_graph ? 1 : 0;
-  out[3] = b->nitems;
+  out[3] = b->nitems[0] + b->nitems[1];
   return LBM_OK;
 }
 

@@ -147,6 +147,9 @@ template <> struct Compute<ST_FP64> { using R = double; };
 // Arithmetic helpers: FP32 uses the fast hardware reciprocal-based divide and
 // power (a few ulp, far below the 1e-5 parity tolerance); FP64 stays exact.
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+// fused multiply-add in the compute type
+__device__ __forceinline__ float fmaf_r(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaf_r(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float pow_sixth(float x) { return __powf(x, 1.0f / 6.0f); }
 __device__ __forceinline__ double pow_sixth(double x) { return pow(x, 1.0 / 6.0); }
@@ -693,6 +696,42 @@ template <class R> __device__ __forceinline__ R relax_delta(R eps) {
 // SCALE: g holds SCALE x h on entry and on return (the raw storage scale of the
 // interior path); the moments are taken back to h once, and the scale enters
 // the equilibrium weights and the force prefactor as constants.
+// Equilibrium of an opposite pair (i, opp i) from per-weight-class coefficients.
+// With s = c_i.u = cU + d (cU = c_x U, d = c_i.du) the deviation equilibrium
+//   h^eq_{i / opp} = w [drho (1 + 4.5 s^2 - 1.5 u.u) + 4.5 d (s + cU) - du15] +/- 3 w (drho s + d)
+// expands into a polynomial in d whose coefficients depend on the weight only:
+//   even part  ev = b2 d^2 + cx c1 d + c0,   odd part  od = d1 d + cx d0,
+//   b2 = 4.5 w rho, c1 = 9 w rho U, c0 = w (drho (1 - 1.5 u.u + 4.5 cx^2 U^2) - du15),
+//   d1 = 3 w rho, d0 = 3 w drho U
+// (two FFMA for ev and one for od, where the expanded form takes seven).
+template <class R> struct EqCoef {
+  R b2, c1, c0x, c00, d1, d0;   // c0x: c0 for c_x != 0; c00: for c_x = 0
+};
+
+template <class R>
+__device__ __forceinline__ EqCoef<R> eq_coef(R wS, R rho, R drho, R U, R one_m_uu15, R du15) {
+  EqCoef<R> k;
+  k.b2 = (R)4.5 * wS * rho;
+  k.c1 = (R)9 * wS * rho * U;
+  k.c00 = wS * (drho * one_m_uu15 - du15);
+  k.c0x = k.c00 + (R)4.5 * wS * drho * U * U;
+  k.d1 = (R)3 * wS * rho;
+  k.d0 = (R)3 * wS * drho * U;
+  return k;
+}
+
+template <int Q, class R>
+__device__ __forceinline__ void eq_pair(const EqCoef<R>& k, int cx, R d, R* ev, R* od) {
+  if (cx == 0) {
+    *ev = fmaf_r(d * d, k.b2, k.c00);
+    *od = k.d1 * d;
+  } else {
+    const R c1 = cx > 0 ? k.c1 : -k.c1, d0 = cx > 0 ? k.d0 : -k.d0;
+    *ev = fmaf_r(d, fmaf_r(d, k.b2, c1), k.c0x);
+    *od = fmaf_r(k.d1, d, d0);
+  }
+}
+
 template <int Q, class R, int SCALE = 1>
 __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* u_out) {
   using L = Lat<Q>;
@@ -729,17 +768,21 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
   u_out[2] = uz;
   const R one_m_uu15 = (R)1 - (R)1.5 * (ux * ux + uy * uy + uz * uz);
   const R du15 = (R)1.5 * (dux * ((R)2 * U + dux) + uy * uy + uz * uz);
+  // equilibrium coefficients of the two weight classes of the moving populations
+  // (index 1: axis directions, index 2: diagonals), storage scale folded in
+  const EqCoef<R> k1 = eq_coef<R>((R)(L::w(1) * SCALE), rho, drho, U, one_m_uu15, du15);
+  const EqCoef<R> k2 = eq_coef<R>((R)(L::w(Q == 19 ? 7 : 5) * SCALE), rho, drho, U, one_m_uu15, du15);
   // (1 - omega/2) w [3 (c - u).F + 9 (c.u)(c.F)] = (delta/2) [A_i (1 + 3 c.u) - 3 w u.F]
   const R fpre = ((R)0.5 * (R)SCALE) * delta;
   const R uF3 = (R)3 * (ux * Fx + uy * Fy + uz * Fz);
+  const R fw1 = fpre * (R)L::w(1) * uF3, fw2 = fpre * (R)L::w(Q == 19 ? 7 : 5) * uF3;
   if (p.collision == 0) {
-    // BGK over opposite pairs (i, i+1 = opp i): with s = c_i.u the equilibrium
-    // and force terms split into parts even and odd in c, so that
-    //   h^eq_{i / opp} = w [drho (e_A +/- 3 s) + (e_D +/- 3 c.du)],
-    //   e_A = 1 + 4.5 s^2 - 1.5 u.u,  e_D = 4.5 c.du (s + c_x U) - du15,
-    //   F_{i / opp} = 3 s A_i - 3 w u.F  +/-  A_i      (A_i = 3 w c_i.F)
-    const R wgt0 = (R)L::w(0);
+    // BGK over opposite pairs: h* = (2 h^eq - h) + delta (h - h^eq) + forcing,
+    // the force term of the pair split into its even part fe and odd part fo,
+    //   F_{i / opp} = fe +/- fo,  fe = fpre (3 s A_i - 3 w u.F),  fo = fpre A_i
+    //   (A_i = 3 w_i c_i.F)
     {
+      const R wgt0 = (R)L::w(0);
       const R geq = (R)(L::w(0) * SCALE) * (drho * one_m_uu15 - du15);
       R gi = ((R)2 * geq - g[0]) + delta * (g[0] - geq);
       if (p.has_force) gi -= fpre * wgt0 * uF3;
@@ -747,21 +790,21 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
-      const R w = (R)L::w(i);
+      const bool diag = L::w(i) < L::w(1);
+      const EqCoef<R>& k = diag ? k2 : k1;
+      const int cx = L::c(i, 0);
       const R cdu = cdot<Q, R>(i, dux, uy, uz);
-      const R cU = L::c(i, 0) > 0 ? U : (L::c(i, 0) < 0 ? -U : (R)0);
-      const R su = cU + cdu;                                   // c_i . u
-      const R eA = (R)4.5 * su * su + one_m_uu15;
-      const R eD = (R)4.5 * cdu * (su + cU) - du15;
-      const R wS = (R)(L::w(i) * SCALE);
-      const R ev = wS * (drho * eA + eD);
-      const R od = wS * (R)3 * (drho * su + cdu);
-      const R gp = ev + od, gm = ev - od;                      // h^eq_i, h^eq_opp
+      R gp, od;
+      eq_pair<Q, R>(k, cx, cdu, &gp, &od);
+      const R gm = gp - od;                                    // h^eq_opp
+      gp += od;                                                // h^eq_i
       R np_ = ((R)2 * gp - g[i]) + delta * (g[i] - gp);
       R nm_ = ((R)2 * gm - g[i + 1]) + delta * (g[i + 1] - gm);
       if (p.has_force) {
-        const R A = psel<R>(p.guoA[i], p.guoA_f[i]);
-        const R fe = fpre * ((R)3 * su * A - w * uF3), fo = fpre * A;
+        const R cU = cx > 0 ? U : (cx < 0 ? -U : (R)0);
+        const R su = cU + cdu;                                 // c_i . u
+        const R fo = fpre * psel<R>(p.guoA[i], p.guoA_f[i]);
+        const R fe = fmaf_r(fo, (R)3 * su, -(diag ? fw2 : fw1));
         np_ += fe + fo;
         nm_ += fe - fo;
       }
@@ -780,13 +823,10 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
   R ax = 0, ay = 0, az = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
-    const R w = (R)L::w(i);
+    const EqCoef<R>& k = L::w(i) < L::w(1) ? k2 : k1;
     const R cdu = cdot<Q, R>(i, dux, uy, uz);
-    const R cU = L::c(i, 0) > 0 ? U : (L::c(i, 0) < 0 ? -U : (R)0);
-    const R su = cU + cdu;
-    const R wS = w * (R)SCALE;
-    const R ev = wS * (drho * ((R)4.5 * su * su + one_m_uu15) + ((R)4.5 * cdu * (su + cU) - du15));
-    const R od = wS * (R)3 * (drho * su + cdu);
+    R ev, od;
+    eq_pair<Q, R>(k, L::c(i, 0), cdu, &ev, &od);
     const R sp = (g[i] + g[i + 1]) - (R)2 * ev;
     const R dp = (g[i] - g[i + 1]) - (R)2 * od;
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
@@ -812,6 +852,7 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     const R w = (R)L::w(i);
+    const bool diag = L::w(i) < L::w(1);
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
     R qp = -tr, ca = 0;
     if (cx) { qp += pxx; ca += cx > 0 ? ax : -ax; }
@@ -823,10 +864,11 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
     R E = g[i] + dm1 * (w * (R)4.5 * qp);
     R O = g[i + 1] + dm1 * (w * (R)3 * ca);
     if (p.has_force) {
-      const R A = psel<R>(p.guoA[i], p.guoA_f[i]);
-      const R su = (cx > 0 ? U : (cx < 0 ? -U : (R)0)) + cdot<Q, R>(i, dux, uy, uz);
-      E += fpre * ((R)3 * su * A - w * uF3);
-      O += fpre * A;
+      const R cU = cx > 0 ? U : (cx < 0 ? -U : (R)0);
+      const R su = cU + cdot<Q, R>(i, dux, uy, uz);
+      const R fo = fpre * psel<R>(p.guoA[i], p.guoA_f[i]);
+      E += fmaf_r(fo, (R)3 * su, -(diag ? fw2 : fw1));
+      O += fo;
     }
     g[i] = E + O;
     g[i + 1] = E - O;
