@@ -533,9 +533,13 @@ static void build_tensor_maps(lbm_ctx* c) {
 }
 
 // Launch shape of k_bulk for a row set (ROWS_ALL / ROWS_INNER / ROWS_WALL).
+// The face-free row sets (the inner rows, every row of a lattice periodic in x
+// and y) run two cells per thread along x.
 void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b) {
+  const bool pairs = rows == ROWS_INNER || (rows == ROWS_ALL && c->base.px && c->base.py);
+  const int nxt = pairs ? (c->nx + 1) / 2 : c->nx;   // threads along x
   int bx = 32;
-  while (bx > 1 && bx / 2 >= c->nx) bx /= 2;
+  while (bx > 1 && bx / 2 >= nxt) bx /= 2;
   const int nrows = rows == ROWS_ALL ? c->ny : (rows == ROWS_WALL ? 2 : c->ny - 2);
   int by = LBM_BULK_THREADS / bx;
   if (rows == ROWS_WALL) by = 2;
@@ -546,7 +550,7 @@ void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b) {
     return;
   }
   *b = dim3(bx, by, 1);
-  *g = dim3((c->nx + bx - 1) / bx, (nrows + by - 1) / by, c->nz);
+  *g = dim3((nxt + bx - 1) / bx, (nrows + by - 1) / by, c->nz);
 }
 
 static void launch_wall(lbm_ctx* c, const Params& p, cudaStream_t s, int prio = 0) {

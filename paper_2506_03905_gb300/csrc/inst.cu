@@ -61,8 +61,10 @@ static void bulk_st(const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, i
   // in-lattice neighbours: the inner rows (whose x-face columns of a
   // non-periodic x axis go to a separate ROWS_XEDGE launch), or every row of
   // a lattice periodic in x and y
+  // (two cells per thread: the launch shape of lbm_ctx_bulk_launch_dims covers
+  // pairs of cells along x for these row sets)
   const bool fast = rows == ROWS_INNER || (rows == ROWS_ALL && p.px && p.py);
-  if (fast) launch_prio(k_bulk<LBM_Q, ST, false>, g, b, s, prio, p, rows);
+  if (fast) launch_prio(k_bulk2<LBM_Q, ST>, g, b, s, prio, p, rows);
   else launch_prio(k_bulk<LBM_Q, ST, true>, g, b, s, prio, p, rows);
 }
 template <int ST>

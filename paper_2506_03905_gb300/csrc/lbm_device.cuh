@@ -116,6 +116,15 @@ template <> struct Codec<ST_FP32> {
   __device__ static __forceinline__ void st(T* p, float v) { *p = v; }
   __device__ static __forceinline__ float ld_raw(const T* p) { return *p; }
   __device__ static __forceinline__ void st_raw(T* p, float v) { *p = v; }
+  // two neighbouring elements p[0], p[1] (p 2-element aligned) in one access
+  __device__ static __forceinline__ void ld2_raw(const T* p, float* a, float* b) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    *a = v.x;
+    *b = v.y;
+  }
+  __device__ static __forceinline__ void st2_raw(T* p, float a, float b) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  }
 };
 template <> struct Codec<ST_FP64> {
   using T = double;
@@ -124,6 +133,14 @@ template <> struct Codec<ST_FP64> {
   __device__ static __forceinline__ void st(T* p, double v) { *p = v; }
   __device__ static __forceinline__ double ld_raw(const T* p) { return *p; }
   __device__ static __forceinline__ void st_raw(T* p, double v) { *p = v; }
+  __device__ static __forceinline__ void ld2_raw(const T* p, double* a, double* b) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    *a = v.x;
+    *b = v.y;
+  }
+  __device__ static __forceinline__ void st2_raw(T* p, double a, double b) {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  }
 };
 template <> struct Codec<ST_FP16> {
   using T = __half;
@@ -132,6 +149,14 @@ template <> struct Codec<ST_FP16> {
   __device__ static __forceinline__ void st(T* p, float v) { *p = __float2half_rn(v * 4096.0f); }
   __device__ static __forceinline__ float ld_raw(const T* p) { return __half2float(*p); }
   __device__ static __forceinline__ void st_raw(T* p, float v) { *p = __float2half_rn(v); }
+  __device__ static __forceinline__ void ld2_raw(const T* p, float* a, float* b) {
+    const __half2 v = *reinterpret_cast<const __half2*>(p);
+    *a = __low2float(v);
+    *b = __high2float(v);
+  }
+  __device__ static __forceinline__ void st2_raw(T* p, float a, float b) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);   // one packed conversion
+  }
 };
 template <> struct Codec<ST_BF16> {
   using T = __nv_bfloat16;
@@ -140,6 +165,14 @@ template <> struct Codec<ST_BF16> {
   __device__ static __forceinline__ void st(T* p, float v) { *p = __float2bfloat16_rn(v); }
   __device__ static __forceinline__ float ld_raw(const T* p) { return __bfloat162float(*p); }
   __device__ static __forceinline__ void st_raw(T* p, float v) { *p = __float2bfloat16_rn(v); }
+  __device__ static __forceinline__ void ld2_raw(const T* p, float* a, float* b) {
+    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(p);
+    *a = __low2float(v);
+    *b = __high2float(v);
+  }
+  __device__ static __forceinline__ void st2_raw(T* p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+  }
 };
 template <int ST> struct Compute { using R = float; };
 template <> struct Compute<ST_FP64> { using R = double; };
@@ -406,19 +439,16 @@ __device__ R sa_update(const Params& p, const R* LBM_RESTRICT v, int x, int y, i
   return nn > (R)0 ? nn : (R)0;
 }
 
-// Same update for a cell whose six neighbours are all inside the lattice
-// (periodic z handled by the plane offsets ozm / ozp); no ghost logic.  One
-// record load per neighbour: x neighbours give nu_tilde, u_y, u_z; y
-// neighbours nu_tilde, u_x, u_z; z neighbours nu_tilde, u_x, u_y.
+// Same update for a cell whose six neighbours are all inside the lattice or
+// periodic, from the seven records of the stencil (no ghost logic): x
+// neighbours give nu_tilde, u_y, u_z; y neighbours nu_tilde, u_x, u_z; z
+// neighbours nu_tilde, u_x, u_y.
 template <class R, bool THREE_D>
-__device__ __forceinline__ R sa_update_interior(const Params& p, const R* LBM_RESTRICT v, int id,
-                                                int oxm, int oxp, int oym, int oyp, int ozm,
-                                                int ozp, int x, int y) {
+__device__ __forceinline__ R sa_core(const Params& p, const Rec<R>& cc, const Rec<R>& xm,
+                                     const Rec<R>& xp, const Rec<R>& ym, const Rec<R>& yp,
+                                     const Rec<R>& zm, const Rec<R>& zp, R inv_d2) {
   const R nu = psel<R>(p.nu, p.nu_f);
   const R h = (R)0.5;
-  const Rec<R> cc = ld_rec(v, id);
-  const Rec<R> xm = ld_rec(v, id + oxm), xp = ld_rec(v, id + oxp);
-  const Rec<R> ym = ld_rec(v, id + oym), yp = ld_rec(v, id + oyp);
   const R c = cc.n;
   R ntm[3], ntp[3];
   ntm[0] = xm.n;
@@ -430,7 +460,6 @@ __device__ __forceinline__ R sa_update_interior(const Params& p, const R* LBM_RE
   R wz = h * ((xp.y - xm.y) - (yp.x - ym.x));
   R S2 = wz * wz;
   if (THREE_D) {
-    const Rec<R> zm = ld_rec(v, id + ozm), zp = ld_rec(v, id + ozp);
     ntm[2] = zm.n;
     ntp[2] = zp.n;
     const R wx = h * ((yp.z - ym.z) - (zp.y - zm.y));
@@ -450,11 +479,27 @@ __device__ __forceinline__ R sa_update_interior(const Params& p, const R* LBM_RE
     const R g = h * (ntp[a] - ntm[a]);
     grad2 += g * g;
   }
-  const R inv_d2 = inv_wall_dist2<R>(p, x, y);
   const R rhs = -conv + sa_source<R>(c, S, psel<R>(p.inv_nu, p.inv_nu_f), inv_d2) +
                 (diff + (R)SAConst::cb2 * grad2) * (R)(1.0 / SAConst::sigma);
   const R nn = c + rhs;
   return nn > (R)0 ? nn : (R)0;
+}
+
+// One cell with in-lattice or periodic neighbours (periodic z handled by the
+// plane offsets ozm / ozp).
+template <class R, bool THREE_D>
+__device__ __forceinline__ R sa_update_interior(const Params& p, const R* LBM_RESTRICT v, int id,
+                                                int oxm, int oxp, int oym, int oyp, int ozm,
+                                                int ozp, int x, int y) {
+  const Rec<R> cc = ld_rec(v, id);
+  const Rec<R> xm = ld_rec(v, id + oxm), xp = ld_rec(v, id + oxp);
+  const Rec<R> ym = ld_rec(v, id + oym), yp = ld_rec(v, id + oyp);
+  Rec<R> zm = cc, zp = cc;
+  if (THREE_D) {
+    zm = ld_rec(v, id + ozm);
+    zp = ld_rec(v, id + ozp);
+  }
+  return sa_core<R, THREE_D>(p, cc, xm, xp, ym, yp, zm, zp, inv_wall_dist2<R>(p, x, y));
 }
 
 // --------------------------------------------------------------------------

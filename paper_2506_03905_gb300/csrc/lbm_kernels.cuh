@@ -93,6 +93,78 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
   interior_finish<Q, ST>(p, o, g, x, y);
 }
 
+// Two neighbouring cells A = (x0, y, z) and B = (x0 + 1, y, z) of one row, x0
+// even, both with in-lattice or periodic neighbours, in one thread: the
+// populations of the directions with c_x = 0 are read for both cells with one
+// paired access, every post-collision pair is written with one, the SA stencil
+// reads 12 records for both cells instead of 14, and the index arithmetic is
+// shared.  Each cell computes exactly what bulk_interior computes.
+template <int Q, int ST>
+__device__ __forceinline__ void bulk_interior2(const Params& p, int x0, int y, int z) {
+  using L = Lat<Q>;
+  using C = Codec<ST>;
+  using R = typename Compute<ST>::R;
+  using T = typename C::T;
+  const T* LBM_RESTRICT fs = (const T*)p.f_src;
+  T* LBM_RESTRICT fd = (T*)p.f_dst;
+  const R* LBM_RESTRICT vs = (const R*)p.v_src;
+  R* LBM_RESTRICT vd = (R*)p.v_dst;
+  const NbOff o = nb_offsets(p, x0, y, z);     // cell A; B has x - 1 = A
+  const int oxpB = x0 + 1 == p.nx - 1 ? -(p.nx - 1) : 1;
+  // pull streaming (Eq. 3) for both cells, issued first
+  R gA[Q], gB[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+    const int yz = (cy > 0 ? o.oym : (cy < 0 ? o.oyp : 0)) + (cz > 0 ? o.ozm : (cz < 0 ? o.ozp : 0));
+    const T* pa = fs + (i * o.nc + o.id + yz);   // element x0 of the source row
+    if (cx == 0) {
+      R a, b;
+      C::ld2_raw(pa, &a, &b);
+      gA[i] = a;
+      gB[i] = b;
+    } else if (cx > 0) {                          // sources x0 - 1 (wrapped) and x0
+      gA[i] = (R)C::ld_raw(pa + o.oxm);
+      gB[i] = (R)C::ld_raw(pa);
+    } else {                                      // sources x0 + 1 and x0 + 2 (wrapped)
+      gA[i] = (R)C::ld_raw(pa + 1);
+      gB[i] = (R)C::ld_raw(pa + 1 + oxpB);
+    }
+  }
+  // SA working variable of the new step (Eq. 11): the records of both stencils
+  R ntA, ntB;
+  const int idB = o.id + 1;
+  if (p.turbulent) {
+    const Rec<R> cA = ld_rec(vs, o.id), cB = ld_rec(vs, idB);
+    const Rec<R> xmA = ld_rec(vs, o.id + o.oxm), xpB = ld_rec(vs, idB + oxpB);
+    const Rec<R> ymA = ld_rec(vs, o.id + o.oym), ymB = ld_rec(vs, idB + o.oym);
+    const Rec<R> ypA = ld_rec(vs, o.id + o.oyp), ypB = ld_rec(vs, idB + o.oyp);
+    Rec<R> zmA = cA, zpA = cA, zmB = cB, zpB = cB;
+    if (Q == 19) {
+      zmA = ld_rec(vs, o.id + o.ozm);
+      zpA = ld_rec(vs, o.id + o.ozp);
+      zmB = ld_rec(vs, idB + o.ozm);
+      zpB = ld_rec(vs, idB + o.ozp);
+    }
+    const R* itab = (const R*)p.invd2 + y * p.pitch + x0;
+    ntA = sa_core<R, (Q == 19)>(p, cA, xmA, cB, ymA, ypA, zmA, zpA, LBM_LDG(itab));
+    ntB = sa_core<R, (Q == 19)>(p, cB, cA, xpB, ymB, ypB, zmB, zpB, LBM_LDG(itab + 1));
+  } else {
+    ntA = vs[4 * o.id + 3];
+    ntB = vs[4 * idB + 3];
+  }
+  const R nu = psel<R>(p.nu, p.nu_f), inu = psel<R>(p.inv_nu, p.inv_nu_f);
+  const R nutA = p.turbulent ? sa_nut<R>(ntA, inu) : (R)0;
+  const R nutB = p.turbulent ? sa_nut<R>(ntB, inu) : (R)0;
+  R uA[3], uB[3];
+  collide<Q, R, C::kScale>(p, gA, relax_delta<R>((R)3 * (nu + nutA)), uA);   // 2 - omega (Eq. 8)
+  collide<Q, R, C::kScale>(p, gB, relax_delta<R>((R)3 * (nu + nutB)), uB);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) C::st2_raw(fd + (i * o.nc + o.id), gA[i], gB[i]);
+  st_rec(vd, o.id, uA[0], uA[1], uA[2], ntA);
+  st_rec(vd, idB, uB[0], uB[1], uB[2], ntB);
+}
+
 // ----------------------------------------------------------------------------
 // Bulk: one thread per cell, x fastest within a warp.  Cells next to a face
 // take the general path with the face rules.
@@ -273,6 +345,29 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
 #pragma unroll
   for (int i = 0; i < Q; ++i) C::st(fd + i * p.ncell + id, g[i]);
   st_rec(vd, id, u[0], u[1], u[2], ntn);
+}
+
+// Face-free rows with two cells per thread (x0 = 2 * thread x index): pairs
+// inside the lattice take bulk_interior2, the lone cell of a row end (odd nx,
+// or a pair cut by the x-face columns of a non-periodic x axis) bulk_interior.
+// Registers: two cells' populations are live at once; the budget is set by
+// LBM_BULK2_MINB blocks of LBM_BULK_THREADS per SM.
+#ifndef LBM_BULK2_MINB
+#define LBM_BULK2_MINB 10
+#endif
+template <int Q, int ST>
+__global__ void __launch_bounds__(LBM_BULK_THREADS, LBM_BULK2_MINB) k_bulk2(const Params p, int rows) {
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int r = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  const int y = rows == ROWS_INNER ? r + 1 : r;
+  if (x0 >= p.nx || y >= (rows == ROWS_INNER ? p.ny - 1 : p.ny)) return;
+  // x-face columns of a non-periodic x axis belong to the ROWS_XEDGE launch
+  const bool inA = p.px || (x0 >= 1 && x0 <= p.nx - 2);
+  const bool inB = x0 + 1 < p.nx && (p.px || x0 + 1 <= p.nx - 2);
+  if (inA && inB) bulk_interior2<Q, ST>(p, x0, y, z);
+  else if (inA) bulk_interior<Q, ST>(p, x0, y, z);
+  else if (inB) bulk_interior<Q, ST>(p, x0 + 1, y, z);
 }
 
 template <int Q, int ST, bool GENERAL>
