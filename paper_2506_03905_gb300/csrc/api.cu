@@ -532,11 +532,22 @@ static void build_tensor_maps(lbm_ctx* c) {
   c->tma_ok = true;
 }
 
+// The face-free row sets (the inner rows, every row of a lattice periodic in x
+// and y) of x-periodic BGK lattices run two cells per thread (k_bulk2).  On the
+// 2048x512x8 plate (regularized collision, inlet and outlet columns) the pair
+// kernel measured slower than one cell per thread (FP32 28.2k vs 29.6k MLUPS,
+// FP16 30.9k vs 32.6k); on the BGK channel faster in FP16 (33.5k vs 31.3k)
+// and equal in FP32.
+bool lbm_ctx_bulk_pairs(const lbm_ctx* c, int rows) {
+  const bool fast = rows == ROWS_INNER || (rows == ROWS_ALL && c->base.px && c->base.py);
+  return LBM_BULK_PAIRS && fast && c->base.px && c->base.collision == 0;
+}
+
 // Launch shape of k_bulk for a row set (ROWS_ALL / ROWS_INNER / ROWS_WALL).
 // The face-free row sets (the inner rows, every row of a lattice periodic in x
 // and y) run two cells per thread along x.
 void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b) {
-  const bool pairs = rows == ROWS_INNER || (rows == ROWS_ALL && c->base.px && c->base.py);
+  const bool pairs = lbm_ctx_bulk_pairs(c, rows);
   const int nxt = pairs ? (c->nx + 1) / 2 : c->nx;   // threads along x
   int bx = 32;
   while (bx > 1 && bx / 2 >= nxt) bx /= 2;
@@ -572,8 +583,9 @@ static void launch_bulk(lbm_ctx* c, const Params& p, int rows, cudaStream_t s, i
   }
   dim3 g, b;
   lbm_ctx_bulk_launch_dims(c, rows, &g, &b);
-  if (c->Q == 9) launch_bulk_q9(c->st, p, rows, g, b, s, prio);
-  else launch_bulk_q19(c->st, p, rows, g, b, s, prio);
+  const bool pairs = lbm_ctx_bulk_pairs(c, rows);
+  if (c->Q == 9) launch_bulk_q9(c->st, p, rows, pairs, g, b, s, prio);
+  else launch_bulk_q19(c->st, p, rows, pairs, g, b, s, prio);
   ++c->launches;
   if (rows == ROWS_INNER && !p.px) launch_bulk(c, p, ROWS_XEDGE, s, prio);   // inlet / outlet columns
 }

@@ -58,16 +58,23 @@ struct BatchInst {
   int itemsA;    // wall pre-pass items of one step
 };
 
-// KIND_I: cells of rows without wall nodes whose six neighbours are all in the
-// lattice or periodic (a channel instance's rows 1..ny-2): the face-free path
+// Item kinds.  KIND_A: a chunk of wall nodes (the wall pre-pass).  KIND_I:
+// cells whose six neighbours are all in the lattice or periodic (the
+// face-free path).  KIND_B: other cells that do not read the wall pre-pass
+// (the x-face columns of a non-periodic x axis, the face rows of a lattice
+// without walls).  KIND_W: the two wall rows, which read what the instance's
+// A items of the same step wrote.
 enum { KIND_A = 0, KIND_B = 1, KIND_W = 2, KIND_I = 3 };
 
+// A cell item covers entries [begin, end) of a box of cells: columns
+// xa + k xs (k < ncol), rows ya + j ys (j < nrow), every z plane, x fastest.
 struct WorkItem {
   int inst;
   int kind;      // KIND_A / KIND_B / KIND_I / KIND_W
   int face;      // KIND_A: 0 = ymin, 1 = ymax
-  int begin, end;   // wall nodes (A) or cells of the item's row set (B, W)
-  int pad[2];
+  int begin, end;   // wall nodes (A) or entries of the box (B, I, W)
+  int xa, xs, ncol, ya, ys, nrow;
+  int pad;
 };
 
 // Control block of one launch of a lattice group, cleared before it: the ticket
@@ -139,18 +146,14 @@ __device__ __forceinline__ void warp_load_params(Params* dst, const Params* src,
 #define LBM_BATCH_BOUNDS __launch_bounds__(256)
 #endif
 
-// Cell (x, y, z) of entry c of an item's row set: B covers rows 1..ny-2 of an
-// instance with walls (every row without), W covers rows 0 and ny-1.
-__device__ __forceinline__ void item_cell(const Params& p, int kind, bool walls, int c, int* x,
-                                          int* y, int* z) {
-  const int nx = p.nx;
-  const int nrow = kind == KIND_W ? 2 : (walls ? p.ny - 2 : p.ny);   // KIND_B / KIND_I
-  const int per_z = nx * nrow;
+// Cell (x, y, z) of entry c of a cell item's box.
+__device__ __forceinline__ void item_cell(const WorkItem& w, int c, int* x, int* y, int* z) {
+  const int per_z = w.ncol * w.nrow;
   *z = c / per_z;
   const int r = c - *z * per_z;
-  const int j = r / nx;
-  *x = r - j * nx;
-  *y = kind == KIND_W ? (j == 0 ? 0 : p.ny - 1) : (walls ? j + 1 : j);
+  const int j = r / w.ncol;
+  *x = w.xa + (r - j * w.ncol) * w.xs;
+  *y = w.ya + j * w.ys;
 }
 
 // One kernel per lattice: the code a warp may run holds one velocity set only
@@ -186,12 +189,18 @@ __global__ void LBM_BATCH_BOUNDS k_batch(BatchInst* inst, const WorkItem* items,
     if (w.kind == KIND_A) {
       for (int node = w.begin + lane; node < w.end; node += 32) wall_node<Q, ST>(p, w.face, node);
     } else {
-      const bool walls = per_a > 0;
-      for (int c = w.begin + lane; c < w.end; c += 32) {
-        int x, y, z;
-        item_cell(p, w.kind, walls, c, &x, &y, &z);
-        if (w.kind == KIND_I) bulk_interior<Q, ST>(p, x, y, z);
-        else bulk_cell<Q, ST, true>(p, x, y, z);
+      if (w.kind == KIND_I) {
+        for (int c = w.begin + lane; c < w.end; c += 32) {
+          int x, y, z;
+          item_cell(w, c, &x, &y, &z);
+          bulk_interior<Q, ST>(p, x, y, z);
+        }
+      } else {
+        for (int c = w.begin + lane; c < w.end; c += 32) {
+          int x, y, z;
+          item_cell(w, c, &x, &y, &z);
+          bulk_cell<Q, ST, true>(p, x, y, z);
+        }
       }
     }
     __syncwarp();
@@ -269,9 +278,18 @@ static void drop_graph(lbm_batch* b) {
 static int group_q(int g) { return g == 0 ? 19 : 9; }
 
 // The items of one step of a lattice group: wall-node chunks of 32 of every
-// instance first, then per instance its ranges of `tile` cells of the rows
-// without wall nodes (face-free when the instance is periodic along x and those
-// rows have in-lattice neighbours along y) and of the wall rows.
+// instance first, then per instance its ranges of `tile` cells: the face-free
+// box (rows 1..ny-2, or every row of a y-periodic lattice without walls, times
+// the columns 1..nx-2, or every column of an x-periodic one), the x-face
+// columns of those rows, and the two face rows (wall rows after the wall
+// pre-pass, KIND_W, or the face rows of a lattice without walls, KIND_B).
+static void push_box(std::vector<WorkItem>& items, int inst, int kind, int tile, int nz, int xa,
+                     int xs, int ncol, int ya, int ys, int nrow) {
+  const int n = ncol * nrow * nz;
+  for (int a = 0; a < n; a += tile)
+    items.push_back({inst, kind, 0, a, std::min(n, a + tile), xa, xs, ncol, ya, ys, nrow, 0});
+}
+
 static void group_items(const lbm_batch* b, int g, int tile, std::vector<WorkItem>& items,
                         std::vector<int>& per_a) {
   std::vector<int> order;
@@ -283,7 +301,7 @@ static void group_items(const lbm_batch* b, int g, int tile, std::vector<WorkIte
       if (!c->base.wall[f]) continue;
       const int nw = c->base.nwall[f];
       for (int a = 0; a < nw; a += 32) {
-        items.push_back({i, KIND_A, f, a, std::min(nw, a + 32), {0, 0}});
+        items.push_back({i, KIND_A, f, a, std::min(nw, a + 32), 0, 0, 0, 0, 0, 0, 0});
         ++per_a[i];
       }
     }
@@ -291,15 +309,16 @@ static void group_items(const lbm_batch* b, int g, int tile, std::vector<WorkIte
   for (int i : order) {
     const lbm_ctx* c = b->ctxs[i];
     const bool walls = per_a[i] > 0;
-    const bool face_free = c->base.px && (walls ? c->ny >= 3 : c->base.py);
-    const int kind = face_free ? KIND_I : KIND_B;
-    const int nb = c->nx * c->nz * (walls ? c->ny - 2 : c->ny);
-    for (int a = 0; a < nb; a += tile) items.push_back({i, kind, 0, a, std::min(nb, a + tile), {0, 0}});
-    if (walls) {
-      const int nwr = 2 * c->nx * c->nz;
-      for (int a = 0; a < nwr; a += tile)
-        items.push_back({i, KIND_W, 0, a, std::min(nwr, a + tile), {0, 0}});
-    }
+    const int nx = c->nx, ny = c->ny, nz = c->nz;
+    const bool px = c->base.px, py = c->base.py && !walls;
+    // face-free rows and columns
+    const int ya = py ? 0 : 1, nrow = py ? ny : std::max(0, ny - 2);
+    const int xa = px ? 0 : 1, ncol = px ? nx : std::max(0, nx - 2);
+    if (ncol > 0 && nrow > 0) push_box(items, i, KIND_I, tile, nz, xa, 1, ncol, ya, 1, nrow);
+    if (!px && nrow > 0)     // x-face columns 0 and nx - 1 of those rows
+      push_box(items, i, KIND_B, tile, nz, 0, nx - 1, nx > 1 ? 2 : 1, ya, 1, nrow);
+    if (!py)                 // face rows 0 and ny - 1
+      push_box(items, i, walls ? KIND_W : KIND_B, tile, nz, 0, 1, nx, 0, ny - 1, ny > 1 ? 2 : 1);
   }
 }
 

@@ -56,15 +56,16 @@ static void bulk_tma_st(const Params& p, const CUtensorMap& tm, int zchunk, cuda
 }
 
 template <int ST>
-static void bulk_st(const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, int prio) {
+static void bulk_st(const Params& p, int rows, bool pairs, dim3 g, dim3 b, cudaStream_t s, int prio) {
   // the face logic is needed unless every cell of the launch has periodic or
   // in-lattice neighbours: the inner rows (whose x-face columns of a
   // non-periodic x axis go to a separate ROWS_XEDGE launch), or every row of
   // a lattice periodic in x and y
-  // (two cells per thread: the launch shape of lbm_ctx_bulk_launch_dims covers
-  // pairs of cells along x for these row sets)
+  // (pairs: two cells per thread, and the launch shape of lbm_ctx_bulk_launch_dims
+  // covers pairs of cells along x)
   const bool fast = rows == ROWS_INNER || (rows == ROWS_ALL && p.px && p.py);
-  if (fast) launch_prio(k_bulk2<LBM_Q, ST>, g, b, s, prio, p, rows);
+  if (fast && pairs) launch_prio(k_bulk2<LBM_Q, ST>, g, b, s, prio, p, rows);
+  else if (fast) launch_prio(k_bulk<LBM_Q, ST, false>, g, b, s, prio, p, rows);
   else launch_prio(k_bulk<LBM_Q, ST, true>, g, b, s, prio, p, rows);
 }
 template <int ST>
@@ -80,8 +81,9 @@ static void wall_st(const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
     default: FN<ST_FP64>(__VA_ARGS__); break;       \
   }
 
-void LBM_QNAME(launch_bulk)(int st, const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s, int prio) {
-  LBM_DISPATCH(bulk_st, p, rows, g, b, s, prio)
+void LBM_QNAME(launch_bulk)(int st, const Params& p, int rows, bool pairs, dim3 g, dim3 b,
+                           cudaStream_t s, int prio) {
+  LBM_DISPATCH(bulk_st, p, rows, pairs, g, b, s, prio)
 }
 void LBM_QNAME(launch_bulk_tma)(int st, const Params& p, const CUtensorMap& tm, int zchunk, cudaStream_t s) {
   LBM_DISPATCH(bulk_tma_st, p, tm, zchunk, s)

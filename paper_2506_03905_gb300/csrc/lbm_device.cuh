@@ -54,6 +54,10 @@ enum { ROWS_ALL = 0, ROWS_INNER = 1, ROWS_WALL = 2, ROWS_XEDGE = 3 };
 #ifndef LBM_BULK_THREADS
 #define LBM_BULK_THREADS 64
 #endif
+// 1: the face-free rows run two cells per thread (k_bulk2); 0: one (k_bulk)
+#ifndef LBM_BULK_PAIRS
+#define LBM_BULK_PAIRS 1
+#endif
 constexpr int RED_THREADS = 256;   // FP64 reduction block size
 constexpr int RED_VALS = 4;        // mass, momentum x/y/z
 

@@ -6,8 +6,8 @@
 
 namespace lbm {
 #define LBM_DECLARE_LAUNCHERS(Q)                                                               \
-  void launch_bulk_q##Q(int st, const Params& p, int rows, dim3 g, dim3 b, cudaStream_t s,     \
-                        int prio);                                                             \
+  void launch_bulk_q##Q(int st, const Params& p, int rows, bool pairs, dim3 g, dim3 b,         \
+                        cudaStream_t s, int prio);                                             \
   void launch_wall_q##Q(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio);    \
   void launch_bulk_tma_q##Q(int st, const Params& p, const CUtensorMap& tm, int zchunk,        \
                             cudaStream_t s);                                                   \
