@@ -237,10 +237,8 @@ lbm_status lbm_run_to_convergence(lbm_ctx* ctx, double tol, int check_every, lon
 
 /* Raw state for checkpointing: the post-collision populations in storage
    precision (bytes reported by lbm_state_bytes), the per-cell records of
-   velocity and nu_tilde (u_x, u_y, u_z, nu_tilde) in compute precision, then
-   per wall face (ymin, ymax) u_tau in FP64, per face the u+ value the Newton
-   inversion carries between steps (FP64), and per face its refresh counters
-   (int), concatenated; a restored state continues bit for bit.  dst and src
+   velocity and nu_tilde (u_x, u_y, u_z, nu_tilde) in compute precision and
+   u_tau in FP64, concatenated.  dst and src
    are host buffers of lbm_state_bytes(ctx) bytes. */
 size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_get_state(lbm_ctx* ctx, void* dst);

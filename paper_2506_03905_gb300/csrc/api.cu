@@ -211,13 +211,10 @@ extern "C" lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     c->v[b] = dalloc(c, (size_t)4 * c->ncell * c->rsz);
     const size_t nodes = (size_t)k.nx * k.nz;
     c->utau[b] = (double*)dalloc(c, nodes * sizeof(double));
-    c->wup[b] = (double*)dalloc(c, nodes * sizeof(double));
-    c->wage[b] = (int*)dalloc(c, nodes * sizeof(int));
     c->uw[b] = dalloc(c, 3 * nodes * c->rsz);
     c->rhow[b] = dalloc(c, nodes * c->rsz);
     c->frec[b] = dalloc(c, (size_t)c->Q * nodes * c->rsz);
-    ok = ok && c->f[b] && c->v[b] && c->utau[b] && c->wup[b] && c->wage[b] && c->uw[b] &&
-         c->rhow[b] && c->frec[b];
+    ok = ok && c->f[b] && c->v[b] && c->utau[b] && c->uw[b] && c->rhow[b] && c->frec[b];
   }
   c->utau_prev = (double*)dalloc(c, 2 * (size_t)k.nx * k.nz * sizeof(double));
   c->invd2 = dalloc(c, (size_t)c->pitch * k.ny * c->rsz);
@@ -417,8 +414,6 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
   }
   for (int b = 0; b < 2; ++b) {
     p.utau[b] = c->utau[b];
-    p.wup[b] = c->wup[b];
-    p.wage[b] = c->wage[b];
     p.uw[b] = c->uw[b];
     p.rhow[b] = c->rhow[b];
     p.frec[b] = c->frec[b];
@@ -660,11 +655,8 @@ extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double
   else
     launch_init_q19(c->st, p, grid, drho, du, dnt, c->cfg.rho0, c->ucv, c->nucv, c->stream);
   ++c->launches;
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < 2; ++b)
     CUDA_TRY(c, cudaMemsetAsync(c->utau[b], 0, (size_t)c->nx * c->nz * sizeof(double), c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->wup[b], 0, (size_t)c->nx * c->nz * sizeof(double), c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->wage[b], 0, (size_t)c->nx * c->nz * sizeof(int), c->stream));
-  }
   CUDA_TRY(c, cudaMemsetAsync(c->utau_prev, 0, 2 * (size_t)c->nx * c->nz * sizeof(double), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * 4, c->stream));
   CUDA_TRY(c, cudaGetLastError());
@@ -967,9 +959,8 @@ extern "C" lbm_status lbm_run_to_convergence(lbm_ctx* c, double tol, int check_e
 
 extern "C" size_t lbm_state_bytes(const lbm_ctx* c) {
   if (!c) return 0;
-  const size_t nodes = (size_t)c->nx * c->nz;
   return (size_t)c->Q * c->ncell * c->esz + (size_t)4 * c->ncell * c->rsz +
-         2 * nodes * (2 * sizeof(double) + sizeof(int));
+         2 * (size_t)c->nx * c->nz * sizeof(double);
 }
 
 extern "C" lbm_status lbm_get_state(lbm_ctx* c, void* dst) {
@@ -983,15 +974,8 @@ extern "C" lbm_status lbm_get_state(lbm_ctx* c, void* dst) {
                wb = (size_t)c->nx * c->nz * sizeof(double);
   CUDA_TRY(c, cudaMemcpyAsync(o, c->f[c->cur], fb, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(o + fb, c->v[c->cur], vb, cudaMemcpyDeviceToHost, c->stream));
-  // per-face blocks after the records: u_tau[0..1], carried u+[0..1], counters[0..1]
-  const size_t ab = (size_t)c->nx * c->nz * sizeof(int);
-  char* q = o + fb + vb;
-  for (int f = 0; f < 2; ++f) {
-    CUDA_TRY(c, cudaMemcpyAsync(q + f * wb, c->utau[f], wb, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(q + (2 + f) * wb, c->wup[f], wb, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(q + 4 * wb + f * ab, c->wage[f], ab, cudaMemcpyDeviceToHost,
-                                c->stream));
-  }
+  CUDA_TRY(c, cudaMemcpyAsync(o + fb + vb, c->utau[0], wb, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(o + fb + vb + wb, c->utau[1], wb, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
@@ -1005,14 +989,8 @@ extern "C" lbm_status lbm_set_state(lbm_ctx* c, const void* src) {
                wb = (size_t)c->nx * c->nz * sizeof(double);
   CUDA_TRY(c, cudaMemcpyAsync(c->f[c->cur], o, fb, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->v[c->cur], o + fb, vb, cudaMemcpyHostToDevice, c->stream));
-  const size_t ab = (size_t)c->nx * c->nz * sizeof(int);
-  const char* q = o + fb + vb;
-  for (int f = 0; f < 2; ++f) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->utau[f], q + f * wb, wb, cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->wup[f], q + (2 + f) * wb, wb, cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->wage[f], q + 4 * wb + f * ab, ab, cudaMemcpyHostToDevice,
-                                c->stream));
-  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->utau[0], o + fb + vb, wb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->utau[1], o + fb + vb + wb, wb, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->flags, 0, sizeof(unsigned) * 4, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->ready = true;

@@ -27,8 +27,6 @@ struct lbm_ctx {
   void* f[2] = {nullptr, nullptr};
   void* v[2] = {nullptr, nullptr};   // SA-field records (u_x, u_y, u_z, nu_tilde) per cell
   double* utau[2] = {nullptr, nullptr};
-  double* wup[2] = {nullptr, nullptr};   // per wall node: carried u+ of the Newton (lbm::Params::wup)
-  int* wage[2] = {nullptr, nullptr};     // per wall node: calls before the next exact wall law
   void* uw[2] = {nullptr, nullptr};
   void* rhow[2] = {nullptr, nullptr};
   void* frec[2] = {nullptr, nullptr};

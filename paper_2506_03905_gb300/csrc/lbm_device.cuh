@@ -238,8 +238,6 @@ struct Params {
   const void* v_src;           // SA-field records (u_x, u_y, u_z, nu_tilde), compute type
   void* v_dst;
   double* utau[2];             // per wall node, FP64 (also the Newton warm start)
-  double* wup[2];              // per wall node: u+ at the reference node for utau (0: unknown)
-  int* wage[2];                // per wall node: calls left before the next exact wall-law value
   void* uw[2];                 // BB: slip velocity (3 per node), compute type
   void* rhow[2];               // BB: wall density, compute type
   void* frec[2];               // HRFD: rebuilt populations (Q per node), deviations, compute type
@@ -534,24 +532,6 @@ __host__ __device__ inline double wf_dudy(int law, double kap, double yp) {
   return (cv3 + ky3) / (cv3 + (1.0 + ky) * ky3);
 }
 
-// Slope and curvature of the wall law at y+ with one division: Eq. 15 is N / D,
-// N = c_v1^3 + (k y)^3, D = N + (k y)^4, so d2u+/dy+2 = (N' - (N/D) D') / D with
-// N' = 3 k (k y)^2, D' = N' + 4 k (k y)^3; the log law gives 1/(k y), -1/(k y^2).
-__host__ __device__ inline void wf_slope2(int law, double kap, double yp, double* d1, double* d2) {
-  if (law == 1) {
-    const double r = 1.0 / (kap * yp);
-    *d1 = r;
-    *d2 = -r / yp;
-    return;
-  }
-  const double k = WF::kappa, ky = k * yp, ky2 = ky * ky, ky3 = ky2 * ky;
-  const double N = WF::cv1 * WF::cv1 * WF::cv1 + ky3, D = N + ky3 * ky;
-  const double Np = 3.0 * k * ky2, Dp = Np + 4.0 * k * ky3;
-  const double inv = 1.0 / D;
-  *d1 = N * inv;
-  *d2 = (Np - *d1 * Dp) * inv;
-}
-
 // The same wall law and slope in FP32, for the wall-function values outside the
 // Newton inversion (u_B of Section 3.1, the slope of Eq. 15 in Eq. 27, the four
 // values of Eq. 29): a few ulp of FP32 (~1e-7 relative), where the FP64 forms
@@ -598,14 +578,10 @@ template <> __device__ __forceinline__ double wf_dudy_r<double>(const Params& p,
 // bar); warm-started from the previous step's u_tau (which moves by far less
 // than 1e-5 per step) this is a single FP64 evaluation of the wall law.  Returns false if the 100-iteration limit was
 // reached (the last iterate is still returned).
-// up_out (optional) receives u+(out y / nu), from the last exact evaluation by a
-// second-order Taylor step (0 if the iteration limit was reached).
 __host__ __device__ inline bool solve_utau(int law, double kap, double B, double U, double y,
-                                           double nu, double guess, double* out,
-                                           double* up_out = nullptr) {
+                                           double nu, double guess, double* out) {
   if (!(U > 0.0)) {
     *out = 0.0;
-    if (up_out) *up_out = 0.0;
     return true;
   }
   double lo = 0.0, hi = 0.0;  // hi == 0: not bracketed from above yet
@@ -616,77 +592,22 @@ __host__ __device__ inline bool solve_utau(int law, double kap, double B, double
     const double g = x * up - U;
     if (g == 0.0) {
       *out = x;
-      if (up_out) *up_out = up;
       return true;
     }
     if (g < 0.0) lo = x; else hi = x;
-    double d1, d2;
-    wf_slope2(law, kap, yp, &d1, &d2);
-    const double dg = up + yp * d1;
+    const double dg = up + yp * wf_dudy(law, kap, yp);
     const double step = g / dg;
     double xn = x - step;
     if (fabs(step) <= 1e-5 * x && xn > 0.0) {
       // quadratic convergence: the error of xn is of order step^2 / x (about 1e-10 x)
       *out = xn;
-      if (up_out) {
-        const double dyp = -step * y / nu;
-        *up_out = up + dyp * (d1 + 0.5 * dyp * d2);
-      }
       return true;
     }
     if (!(xn > lo) || (hi > 0.0 && !(xn < hi)) || !(dg > 0.0)) xn = hi > 0.0 ? 0.5 * (lo + hi) : 2.0 * x;
     x = xn;
   }
   *out = x;
-  if (up_out) *up_out = 0.0;
   return false;
-}
-
-// Calls of the wall pass between exact wall-law evaluations at one node.
-constexpr int kWallRefresh = 16;
-
-// The same FP64 Newton with the wall-law value carried from step to step.  The
-// node's state is its accepted u_tau (*ut), u+ at that u_tau (*up, 0 when
-// unknown) and the calls left before the next exact evaluation (*age).  While
-// u_tau moves by less than 1e-5 of itself per step, the Newton step from the
-// carried value is accepted, and u+ at the new u_tau follows by a second-order
-// Taylor step: only the rational Eq. 15 and its derivative are evaluated, no
-// logarithm or arctangent (on GB300 those run on the FP64 pipe at 1/64 of the
-// FP32 rate).  The Taylor remainder is of order (1e-5)^3 of u+ per step.
-// Every kWallRefresh-th call, after a larger step or with no carried value the
-// wall law is evaluated exactly (solve_utau); `stagger` (0 <= stagger <
-// kWallRefresh) offsets the first refresh so that nodes refresh on different
-// steps.
-__host__ __device__ inline bool solve_utau_carry(int law, double kap, double B, double U, double y,
-                                                 double nu, double* ut, double* up, int* age,
-                                                 int stagger) {
-  if (!(U > 0.0)) {
-    *ut = 0.0;
-    *up = 0.0;
-    *age = 0;
-    return true;
-  }
-  const double x = *ut;
-  if (x > 0.0 && *up > 0.0 && *age > 0) {
-    const double yp = x * y / nu, upx = *up;
-    double d1, d2;
-    wf_slope2(law, kap, yp, &d1, &d2);
-    const double g = x * upx - U, dg = upx + yp * d1;
-    const double step = g / dg, xn = x - step;
-    if (dg > 0.0 && fabs(step) <= 1e-5 * x && xn > 0.0) {
-      const double dyp = -step * y / nu;
-      *up = upx + dyp * (d1 + 0.5 * dyp * d2);
-      *ut = xn;
-      *age -= 1;
-      return true;
-    }
-  }
-  double xn = 0.0, upn = 0.0;
-  const bool ok = solve_utau(law, kap, B, U, y, nu, x, &xn, &upn);
-  *age = *up > 0.0 ? kWallRefresh - 1 : stagger;
-  *ut = xn;
-  *up = upn;
-  return ok;
 }
 
 // f_i^eq(rho, u) - E_i written in the small quantities drho = rho - 1 and

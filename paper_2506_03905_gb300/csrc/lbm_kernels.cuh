@@ -569,10 +569,9 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const R iU = Um > (R)0 ? (R)1 / Um : (R)0;
     const R tx = Um > (R)0 ? Ux * iU : (R)1, tz = Uz * iU;
     R* uw = (R*)p.uw[fi] + 3 * node;
+    if (!isfinite(Um)) atomicOr(p.flags, FLAG_NONFINITE);   // reported, not turned into u_tau = 0
     if (p.turbulent) {
-      ut = p.utau[fi][node];
-      ok = solve_utau_carry(p.wall_law, p.law_kappa, p.law_B, (double)Um, yref, nu, &ut,
-                            &p.wup[fi][node], &p.wage[fi][node], node % kWallRefresh);
+      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, (double)Um, yref, nu, p.utau[fi][node], &ut);
       const R utr = (R)ut, nur = psel<R>(p.nu, p.nu_f), kap = (R)WF::kappa;
       const R ypB = utr * (R)dw * psel<R>(p.inv_nu, p.inv_nu_f);
       // Eq. 35 with Delta_w = y_B = d_w and nu_t|_B = nu kappa y_B+
@@ -609,11 +608,10 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const R iU = Um > (R)0 ? (R)1 / Um : (R)0;
     const R tx = Um > (R)0 ? Ux * iU : (R)1, tz = Uz * iU;
     const double dw = p.d_w[fi];                       // y_B; y_F = 1 + d_w
-    if (p.turbulent) {
-      ut = p.utau[fi][node];
-      ok = solve_utau_carry(p.wall_law, p.law_kappa, p.law_B, (double)Um, 1.0 + dw, nu, &ut,
-                            &p.wup[fi][node], &p.wage[fi][node], node % kWallRefresh);
-    }
+    if (!isfinite(Um)) atomicOr(p.flags, FLAG_NONFINITE);
+    if (p.turbulent)
+      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, (double)Um, 1.0 + dw, nu, p.utau[fi][node],
+                      &ut);
     const R utr = (R)ut, inu = psel<R>(p.inv_nu, p.inv_nu_f);
     const R ypB = utr * (R)dw * inu;
     const R upB = p.turbulent ? utr * wf_uplus_r<R>(p, ypB) : (R)0;   // u_B = u_tau u+(y_B+)
