@@ -610,6 +610,53 @@ __host__ __device__ inline bool solve_utau(int law, double kap, double B, double
   return false;
 }
 
+// The same root with the iterations shared between FP32 and FP64.  Newton runs
+// in FP32 from the warm start (the FP32 wall law: logf, atan2f) until its step
+// is below 1e-5 of the iterate, which FP32 resolves; one Newton step in FP64
+// with the exact FP64 wall law then completes the inversion (quadratic
+// convergence: the FP32 iterate is within ~1e-6 of the root, the FP64 step
+// leaves ~1e-12).  A developing flow, whose u_tau moves by more than 1e-5 per
+// step, thereby costs one FP64 evaluation of Eq. 16 per node and step instead
+// of two; on GB300 the FP64 logarithms and arctangents run at 1/64 of the FP32
+// rate.  Falls back to the FP64 iteration (solve_utau) if the FP32 one does not
+// settle or the FP64 step is not small.
+__device__ inline bool solve_utau_mixed(int law, double kap, double B, double U, double y,
+                                        double nu, double guess, double* out) {
+  if (!(U > 0.0)) {
+    *out = 0.0;
+    return true;
+  }
+  const float Uf = (float)U, yn = (float)(y / nu), kf = (float)kap, Bf = (float)B;
+  float xf = guess > 0.0 ? (float)guess : sqrtf(Uf / yn);
+  bool settled = false;
+  for (int it = 0; it < 8; ++it) {
+    const float yp = xf * yn;
+    const float up = wf_uplus_f(law, kf, Bf, yp);
+    const float dg = up + yp * wf_dudy_f(law, kf, yp);
+    const float step = (xf * up - Uf) / dg;
+    const float xn = xf - step;
+    if (!(dg > 0.0f) || !(xn > 0.0f)) break;
+    xf = xn;
+    if (fabsf(step) <= 1e-5f * xf) {
+      settled = true;
+      break;
+    }
+  }
+  const double x = settled ? (double)xf : guess;
+  if (settled) {
+    const double yp = x * y / nu;
+    const double up = wf_uplus(law, kap, B, yp);
+    const double dg = up + yp * wf_dudy(law, kap, yp);
+    const double step = (x * up - U) / dg;
+    const double xn = x - step;
+    if (dg > 0.0 && fabs(step) <= 1e-4 * x && xn > 0.0) {
+      *out = xn;
+      return true;
+    }
+  }
+  return solve_utau(law, kap, B, U, y, nu, x, out);
+}
+
 // f_i^eq(rho, u) - E_i written in the small quantities drho = rho - 1 and
 // du = u - U x (u = U x + du):
 //   w [drho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u) + 3 c.du + 4.5 c.du (2 c_x U + c.du)

@@ -571,7 +571,8 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     R* uw = (R*)p.uw[fi] + 3 * node;
     if (!isfinite(Um)) atomicOr(p.flags, FLAG_NONFINITE);   // reported, not turned into u_tau = 0
     if (p.turbulent) {
-      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, (double)Um, yref, nu, p.utau[fi][node], &ut);
+      ok = solve_utau_mixed(p.wall_law, p.law_kappa, p.law_B, (double)Um, yref, nu, p.utau[fi][node],
+                            &ut);
       const R utr = (R)ut, nur = psel<R>(p.nu, p.nu_f), kap = (R)WF::kappa;
       const R ypB = utr * (R)dw * psel<R>(p.inv_nu, p.inv_nu_f);
       // Eq. 35 with Delta_w = y_B = d_w and nu_t|_B = nu kappa y_B+
@@ -610,7 +611,7 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const double dw = p.d_w[fi];                       // y_B; y_F = 1 + d_w
     if (!isfinite(Um)) atomicOr(p.flags, FLAG_NONFINITE);
     if (p.turbulent)
-      ok = solve_utau(p.wall_law, p.law_kappa, p.law_B, (double)Um, 1.0 + dw, nu, p.utau[fi][node],
+      ok = solve_utau_mixed(p.wall_law, p.law_kappa, p.law_B, (double)Um, 1.0 + dw, nu, p.utau[fi][node],
                       &ut);
     const R utr = (R)ut, inu = psel<R>(p.inv_nu, p.inv_nu_f);
     const R ypB = utr * (R)dw * inu;
