@@ -205,6 +205,12 @@ extern "C" lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     delete c;
     return LBM_ECUDA;
   }
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      c->sms = sms;
+  }
   bool ok = true;
   for (int b = 0; b < 2; ++b) {
     c->f[b] = dalloc(c, (size_t)c->Q * c->ncell * c->esz);
@@ -538,8 +544,11 @@ static void build_tensor_maps(lbm_ctx* c) {
 // kernel measured slower than one cell per thread (FP32 28.2k vs 29.6k MLUPS,
 // FP16 30.9k vs 32.6k); on the BGK channel faster in FP16 (33.5k vs 31.3k)
 // and equal in FP32.
+// Which face-free row sets run two cells per thread: LBM_BULK_PAIRS 1, those of
+// lattices periodic in x with BGK collision; 2, every one.
 bool lbm_ctx_bulk_pairs(const lbm_ctx* c, int rows) {
   const bool fast = rows == ROWS_INNER || (rows == ROWS_ALL && c->base.px && c->base.py);
+  if (LBM_BULK_PAIRS >= 2) return fast;
   return LBM_BULK_PAIRS && fast && c->base.px && c->base.collision == 0;
 }
 
@@ -564,9 +573,25 @@ void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b) {
   *g = dim3((nxt + bx - 1) / bx, (nrows + by - 1) / by, c->nz);
 }
 
+// Bounce-back wall passes take LBM_WALL_BLOCKS_PER_SM blocks of 128 threads per
+// SM at most, shared between the wall faces, and their blocks stride over the
+// nodes: the FP64 Newton bounds them, a few warps per SM keep that pipe busy,
+// and the registers they leave free stay with the inner rows running beside
+// them (on the 256x128x128 channel, 0.1304 ms per step against 0.1318 ms with
+// one thread per node).  Regularized passes, bound by the latency of their
+// gathers, keep one thread per node (capped to 1 and 2 blocks per SM their
+// step took 0.224 and 0.168 ms against 0.151 ms).
+#ifndef LBM_WALL_BLOCKS_PER_SM
+#define LBM_WALL_BLOCKS_PER_SM 2
+#endif
+
 static void launch_wall(lbm_ctx* c, const Params& p, cudaStream_t s, int prio = 0) {
   const int maxw = std::max(p.wall[0] ? p.nwall[0] : 0, p.wall[1] ? p.nwall[1] : 0);
-  dim3 g((maxw + 127) / 128, 2, 1), b(128, 1, 1);
+  const int faces = (p.wall[0] ? 1 : 0) + (p.wall[1] ? 1 : 0);
+  const bool regularized = (p.wall[0] && p.wall[0] != BC_WALL_BB) || (p.wall[1] && p.wall[1] != BC_WALL_BB);
+  int gx = (maxw + 127) / 128;
+  if (!regularized) gx = std::min(gx, std::max(1, c->sms * LBM_WALL_BLOCKS_PER_SM / std::max(faces, 1)));
+  dim3 g(gx, 2, 1), b(128, 1, 1);
   if (c->Q == 9) launch_wall_q9(c->st, p, g, b, s, prio);
   else launch_wall_q19(c->st, p, g, b, s, prio);
   ++c->launches;

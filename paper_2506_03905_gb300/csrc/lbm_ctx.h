@@ -24,6 +24,7 @@ struct lbm_ctx {
   cudaStream_t side_stream = nullptr;  // wall pre-pass branch of a step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int prio_hi = 0;                     // greatest stream priority of the device
+  int sms = 152;                       // streaming multiprocessors of the device
   void* f[2] = {nullptr, nullptr};
   void* v[2] = {nullptr, nullptr};   // SA-field records (u_x, u_y, u_z, nu_tilde) per cell
   double* utau[2] = {nullptr, nullptr};

@@ -18,6 +18,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 // Loads of the population and SA-field buffers.  The step kernels read buffers
 // that no thread of the same launch writes, so they mark their pointers
 // __restrict__ and read the records through the read-only path.  A persistent
@@ -195,6 +197,66 @@ __device__ __forceinline__ float nn_sqrt(float x) { return x > 0.0f ? x * rsqrtf
 __device__ __forceinline__ double nn_sqrt(double x) { return sqrt(x); }
 
 // --------------------------------------------------------------------------
+// Two FP32 lanes in one value: cell A in .x, cell B in .y.  Sums, products and
+// fused multiply-adds issue as one packed instruction for both lanes (add /
+// mul / fma on .f32x2, sm_100 and later); each lane is rounded exactly as the
+// scalar instruction rounds it.  Divisions, square roots and powers have no
+// packed form and run per lane.  The two-cells-per-thread kernels compute on
+// this type, which halves their issued FP32 arithmetic.
+// --------------------------------------------------------------------------
+struct f2 {
+  float2 v;
+  f2() = default;
+  __device__ __forceinline__ f2(float a) : v(make_float2(a, a)) {}
+  __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ __forceinline__ explicit f2(float2 a) : v(a) {}
+  __device__ __forceinline__ explicit f2(double a) : v(make_float2((float)a, (float)a)) {}
+  __device__ __forceinline__ explicit f2(int a) : v(make_float2((float)a, (float)a)) {}
+};
+__device__ __forceinline__ f2 operator-(f2 a) { return f2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__fadd2_rn(a.v, (-b).v)); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2& operator+=(f2& a, f2 b) { return a = a + b; }
+__device__ __forceinline__ f2& operator-=(f2& a, f2 b) { return a = a - b; }
+__device__ __forceinline__ f2& operator*=(f2& a, f2 b) { return a = a * b; }
+__device__ __forceinline__ f2 fmaf_r(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
+// a / b: one approximate reciprocal per lane, the product packed
+__device__ __forceinline__ f2 fdiv(f2 a, f2 b) {
+  return a * f2(__fdividef(1.0f, b.v.x), __fdividef(1.0f, b.v.y));
+}
+__device__ __forceinline__ f2 pow_sixth(f2 x) { return f2(pow_sixth(x.v.x), pow_sixth(x.v.y)); }
+__device__ __forceinline__ f2 nn_sqrt(f2 x) {
+  const f2 r(x.v.x > 0.0f ? rsqrtf(x.v.x) : 0.0f, x.v.y > 0.0f ? rsqrtf(x.v.y) : 0.0f);
+  return x * r;
+}
+
+// Per-lane comparisons and selections of the compute types (float, double, f2).
+// sel_pos(c, a, b) = c > 0 ? a : b; pos_part(x) = x > 0 ? x : 0;
+// min_lt(q, r) = q < r ? q : r; all_ge(a, b): a >= b in every lane;
+// sel_ge(a, b, x, y) = a >= b ? x : y; any_pos(x): x > 0 in some lane.
+template <class R> __device__ __forceinline__ R sel_pos(R c, R a, R b) { return c > (R)0 ? a : b; }
+template <class R> __device__ __forceinline__ R pos_part(R x) { return x > (R)0 ? x : (R)0; }
+template <class R> __device__ __forceinline__ R min_lt(R q, R r) { return q < r ? q : r; }
+template <class R> __device__ __forceinline__ bool all_ge(R a, R b) { return a >= b; }
+template <class R> __device__ __forceinline__ R sel_ge(R a, R b, R x, R y) { return a >= b ? x : y; }
+template <class R> __device__ __forceinline__ bool any_pos(R x) { return x > (R)0; }
+template <> __device__ __forceinline__ f2 sel_pos(f2 c, f2 a, f2 b) {
+  return f2(c.v.x > 0.0f ? a.v.x : b.v.x, c.v.y > 0.0f ? a.v.y : b.v.y);
+}
+template <> __device__ __forceinline__ f2 pos_part(f2 x) {
+  return f2(x.v.x > 0.0f ? x.v.x : 0.0f, x.v.y > 0.0f ? x.v.y : 0.0f);
+}
+template <> __device__ __forceinline__ f2 min_lt(f2 q, f2 r) {
+  return f2(q.v.x < r.v.x ? q.v.x : r.v.x, q.v.y < r.v.y ? q.v.y : r.v.y);
+}
+template <> __device__ __forceinline__ bool all_ge(f2 a, f2 b) { return a.v.x >= b.v.x && a.v.y >= b.v.y; }
+template <> __device__ __forceinline__ f2 sel_ge(f2 a, f2 b, f2 x, f2 y) {
+  return f2(a.v.x >= b.v.x ? x.v.x : y.v.x, a.v.y >= b.v.y ? x.v.y : y.v.y);
+}
+template <> __device__ __forceinline__ bool any_pos(f2 x) { return x.v.x > 0.0f || x.v.y > 0.0f; }
+
+// --------------------------------------------------------------------------
 // Kernel parameters (lattice units), passed by value.
 // --------------------------------------------------------------------------
 struct Params {
@@ -240,7 +302,7 @@ struct Params {
   double* utau[2];             // per wall node, FP64 (also the Newton warm start)
   void* uw[2];                 // BB: slip velocity (3 per node), compute type
   void* rhow[2];               // BB: wall density, compute type
-  void* frec[2];               // HRFD: rebuilt populations (Q per node), deviations, compute type
+  void* frec[2];               // HRFD: rebuilt populations [i][node], deviations, compute type
   const void* invd2;           // 1 / d^2 (wall distance of the SA model), compute type, [y][x]
   unsigned* flags;
   long long wait_limit;        // polls of a bounded device-side wait before it gives up
@@ -250,6 +312,7 @@ struct Params {
 template <class R> __device__ __forceinline__ R psel(double d, float f);
 template <> __device__ __forceinline__ float psel<float>(double, float f) { return f; }
 template <> __device__ __forceinline__ double psel<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ f2 psel<f2>(double, float f) { return f2(f); }
 
 // SA-field record of a cell: the velocity and nu_tilde, stored together (16 B
 // in FP32, 32 B in FP64).  ld_rec reads a record of the source buffer with one
@@ -291,12 +354,6 @@ struct SAConst {
   static constexpr double cv2lim = 0.7, cv3lim = 0.9;
 };
 
-template <class R> __device__ __forceinline__ R sa_fv1(R chi) {
-  const R c3 = chi * chi * chi;
-  const R cv = (R)SAConst::cv1;
-  return c3 / (c3 + cv * cv * cv);
-}
-
 // nu_t = nu_tilde f_v1(nu_tilde / nu) (Eq. 10); inv_nu = 1 / nu
 template <class R> __device__ __forceinline__ R sa_nut(R nt, R inv_nu) {
   const R chi = nt * inv_nu;
@@ -306,31 +363,27 @@ template <class R> __device__ __forceinline__ R sa_nut(R nt, R inv_nu) {
 
 // P - D of Eq. 12 with S~ (Eq. 13, kept positive by the ICCFD7 limiter) and r, f_w (Eq. 14)
 template <class R> __device__ __forceinline__ R sa_source(R nt, R S, R inv_nu, R inv_d2) {
-  const R kap = (R)SAConst::kappa;
-  const R cw1 = (R)SAConst::cb1 / (kap * kap) + ((R)1 + (R)SAConst::cb2) / (R)SAConst::sigma;
+  constexpr double k2 = SAConst::kappa * SAConst::kappa;
+  const R cw1 = (R)(SAConst::cb1 / k2 + (1.0 + SAConst::cb2) / SAConst::sigma);
   const R chi = nt * inv_nu;
   const R c3 = chi * chi * chi;
   const R fv1 = fdiv(c3, c3 + (R)(SAConst::cv1 * SAConst::cv1 * SAConst::cv1));
   const R fv2 = (R)1 - fdiv(chi, (R)1 + chi * fv1);
-  const R inv_kd2 = inv_d2 * ((R)1 / (kap * kap));
+  const R inv_kd2 = inv_d2 * (R)(1.0 / k2);
   const R sbar = nt * fv2 * inv_kd2;
-  R st;
-  if (sbar >= -(R)SAConst::cv2lim * S) {
-    st = S + sbar;
-  } else {
-    st = S + fdiv(S * ((R)(SAConst::cv2lim * SAConst::cv2lim) * S + (R)SAConst::cv3lim * sbar),
-                  ((R)SAConst::cv3lim - (R)2 * (R)SAConst::cv2lim) * S - sbar);
-  }
+  const R lim = -(R)SAConst::cv2lim * S;
+  R st = S + sbar;
+  if (!all_ge(sbar, lim))
+    st = sel_ge(sbar, lim, st,
+                S + fdiv(S * ((R)(SAConst::cv2lim * SAConst::cv2lim) * S + (R)SAConst::cv3lim * sbar),
+                         (R)(SAConst::cv3lim - 2.0 * SAConst::cv2lim) * S - sbar));
   R r = (R)SAConst::rlim;
-  if (st > (R)0) {
-    const R q = fdiv(nt * inv_kd2, st);
-    r = q < r ? q : r;
-  }
+  if (any_pos(st)) r = sel_pos(st, min_lt(fdiv(nt * inv_kd2, st), r), r);
   const R r2 = r * r, r6 = r2 * r2 * r2;
   const R g = r + (R)SAConst::cw2 * (r6 - r);
   const R g2 = g * g, g6 = g2 * g2 * g2;
   const R cw36 = (R)64;  // c_w3^6
-  const R fw = g * pow_sixth(fdiv((R)1 + cw36, g6 + cw36));
+  const R fw = g * pow_sixth(fdiv((R)65, g6 + cw36));   // (1 + c_w3^6) / (g^6 + c_w3^6)
   return (R)SAConst::cb1 * st * nt - cw1 * fw * nt * nt * inv_d2;
 }
 
@@ -478,15 +531,14 @@ __device__ __forceinline__ R sa_core(const Params& p, const Rec<R>& cc, const Re
   R conv = 0, diff = 0, grad2 = 0;
 #pragma unroll
   for (int a = 0; a < (THREE_D ? 3 : 2); ++a) {
-    conv += ua[a] > (R)0 ? ua[a] * (c - ntm[a]) : ua[a] * (ntp[a] - c);
+    conv += ua[a] * sel_pos(ua[a], c - ntm[a], ntp[a] - c);
     diff += (nu + h * (c + ntp[a])) * (ntp[a] - c) - (nu + h * (c + ntm[a])) * (c - ntm[a]);
     const R g = h * (ntp[a] - ntm[a]);
     grad2 += g * g;
   }
   const R rhs = -conv + sa_source<R>(c, S, psel<R>(p.inv_nu, p.inv_nu_f), inv_d2) +
                 (diff + (R)SAConst::cb2 * grad2) * (R)(1.0 / SAConst::sigma);
-  const R nn = c + rhs;
-  return nn > (R)0 ? nn : (R)0;
+  return pos_part(c + rhs);
 }
 
 // One cell with in-lattice or periodic neighbours (periodic z handled by the
@@ -843,7 +895,7 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
     if (L::c(i, 2)) jz += L::c(i, 2) > 0 ? dp : -dp;
   }
   if (SCALE != 1) {
-    const R is = (R)1 / (R)SCALE;
+    const R is = (R)(1.0 / SCALE);
     drho *= is;
     jx *= is;
     jy *= is;
@@ -938,7 +990,7 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
     g[i] = ev;       // the equilibrium parts are all the rebuild needs
     g[i + 1] = od;
   }
-  const R tr = (pxx + pyy + pzz) * ((R)1 / (R)3);
+  const R tr = (pxx + pyy + pzz) * (R)(1.0 / 3.0);
   {
     const R wgt0 = (R)L::w(0);
     R gi = (wgt0 * (R)SCALE) * (drho * one_m_uu15 - du15) + dm1 * (wgt0 * (R)4.5 * -tr);

@@ -41,6 +41,20 @@ __device__ __forceinline__ NbOff nb_offsets(const Params& p, int x, int y, int z
   return o;
 }
 
+// Post-stream deviation g_i (storage scale removed) at the cell of o, for a
+// source inside the lattice or across a periodic face: the neighbour offsets
+// stand in for the face logic of pull_bc.
+template <int Q, int ST>
+__device__ __forceinline__ typename Compute<ST>::R pull_nb(const Params& p, const NbOff& o, int i) {
+  using L = Lat<Q>;
+  using C = Codec<ST>;
+  using T = typename C::T;
+  const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+  const int off = (cx > 0 ? o.oxm : (cx < 0 ? o.oxp : 0)) + (cy > 0 ? o.oym : (cy < 0 ? o.oyp : 0)) +
+                  (cz > 0 ? o.ozm : (cz < 0 ? o.ozp : 0));
+  return (typename Compute<ST>::R)C::ld((const T*)p.f_src + (i * o.nc + o.id + off));
+}
+
 // Everything after streaming for a cell with in-lattice (or periodic)
 // neighbours: SA update, relaxation rate, collision, stores.  g holds the
 // pulled populations in the raw storage scale (Codec::ld_raw).
@@ -104,6 +118,13 @@ __device__ __forceinline__ void bulk_interior2(const Params& p, int x0, int y, i
   using L = Lat<Q>;
   using C = Codec<ST>;
   using R = typename Compute<ST>::R;
+  // FP32 arithmetic of the pair on packed lanes (f2); FP64 as two scalars
+  using V = typename std::conditional<std::is_same<R, float>::value, f2, R>::type;
+  constexpr bool kPacked = std::is_same<V, f2>::value;
+  // the SA stencil on packed lanes too for 16-bit storage (measured 0.1148 against
+  // 0.1168 ms per step, FP16 channel 256x128x128); FP32 storage keeps it scalar,
+  // whose registers fit the budget (packed: 0.1334 against 0.1252 ms, spilling)
+  constexpr bool kPackedSA = kPacked && ST != ST_FP32;
   using T = typename C::T;
   const T* LBM_RESTRICT fs = (const T*)p.f_src;
   T* LBM_RESTRICT fd = (T*)p.f_dst;
@@ -147,22 +168,48 @@ __device__ __forceinline__ void bulk_interior2(const Params& p, int x0, int y, i
       zpB = ld_rec(vs, idB + o.ozp);
     }
     const R* itab = (const R*)p.invd2 + y * p.pitch + x0;
-    ntA = sa_core<R, (Q == 19)>(p, cA, xmA, cB, ymA, ypA, zmA, zpA, LBM_LDG(itab));
-    ntB = sa_core<R, (Q == 19)>(p, cB, cA, xpB, ymB, ypB, zmB, zpB, LBM_LDG(itab + 1));
+    if constexpr (kPackedSA) {
+      // lanes (A, B) of each stencil position: x - 1 of B is A, x + 1 of A is B
+      const auto pk = [](const Rec<float>& a, const Rec<float>& b) {
+        return Rec<f2>{f2(a.x, b.x), f2(a.y, b.y), f2(a.z, b.z), f2(a.n, b.n)};
+      };
+      const float2 id2 = LBM_LDG(reinterpret_cast<const float2*>(itab));
+      const f2 nt = sa_core<f2, (Q == 19)>(p, pk(cA, cB), pk(xmA, cA), pk(cB, xpB), pk(ymA, ymB),
+                                           pk(ypA, ypB), pk(zmA, zmB), pk(zpA, zpB), f2(id2));
+      ntA = nt.v.x;
+      ntB = nt.v.y;
+    } else {
+      ntA = sa_core<R, (Q == 19)>(p, cA, xmA, cB, ymA, ypA, zmA, zpA, LBM_LDG(itab));
+      ntB = sa_core<R, (Q == 19)>(p, cB, cA, xpB, ymB, ypB, zmB, zpB, LBM_LDG(itab + 1));
+    }
   } else {
     ntA = vs[4 * o.id + 3];
     ntB = vs[4 * idB + 3];
   }
-  const R nu = psel<R>(p.nu, p.nu_f), inu = psel<R>(p.inv_nu, p.inv_nu_f);
-  const R nutA = p.turbulent ? sa_nut<R>(ntA, inu) : (R)0;
-  const R nutB = p.turbulent ? sa_nut<R>(ntB, inu) : (R)0;
-  R uA[3], uB[3];
-  collide<Q, R, C::kScale>(p, gA, relax_delta<R>((R)3 * (nu + nutA)), uA);   // 2 - omega (Eq. 8)
-  collide<Q, R, C::kScale>(p, gB, relax_delta<R>((R)3 * (nu + nutB)), uB);
+  if constexpr (kPacked) {
+    f2 g[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) C::st2_raw(fd + (i * o.nc + o.id), gA[i], gB[i]);
-  st_rec(vd, o.id, uA[0], uA[1], uA[2], ntA);
-  st_rec(vd, idB, uB[0], uB[1], uB[2], ntB);
+    for (int i = 0; i < Q; ++i) g[i] = f2(gA[i], gB[i]);
+    const f2 nt(ntA, ntB), nu = psel<f2>(p.nu, p.nu_f), inu = psel<f2>(p.inv_nu, p.inv_nu_f);
+    const f2 nut = p.turbulent ? sa_nut<f2>(nt, inu) : f2(0.0f);
+    f2 u[3];
+    collide<Q, f2, C::kScale>(p, g, relax_delta<f2>(f2(3.0f) * (nu + nut)), u);   // 2 - omega (Eq. 8)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) C::st2_raw(fd + (i * o.nc + o.id), g[i].v.x, g[i].v.y);
+    st_rec(vd, o.id, u[0].v.x, u[1].v.x, u[2].v.x, ntA);
+    st_rec(vd, idB, u[0].v.y, u[1].v.y, u[2].v.y, ntB);
+  } else {
+    const R nu = psel<R>(p.nu, p.nu_f), inu = psel<R>(p.inv_nu, p.inv_nu_f);
+    const R nutA = p.turbulent ? sa_nut<R>(ntA, inu) : (R)0;
+    const R nutB = p.turbulent ? sa_nut<R>(ntB, inu) : (R)0;
+    R uA[3], uB[3];
+    collide<Q, R, C::kScale>(p, gA, relax_delta<R>((R)3 * (nu + nutA)), uA);   // 2 - omega (Eq. 8)
+    collide<Q, R, C::kScale>(p, gB, relax_delta<R>((R)3 * (nu + nutB)), uB);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) C::st2_raw(fd + (i * o.nc + o.id), gA[i], gB[i]);
+    st_rec(vd, o.id, uA[0], uA[1], uA[2], ntA);
+    st_rec(vd, idB, uB[0], uB[1], uB[2], ntB);
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -296,9 +343,9 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
   R g[Q];
   if (wf >= 0 && p.wall[wf] != BC_WALL_BB) {   // regularized wall: rebuilt populations
     const int node = z * (p.nx - p.xw0[wf]) + (x - p.xw0[wf]);
-    const R* fr = (const R*)p.frec[wf] + (long long)node * Q;
+    const R* fr = (const R*)p.frec[wf] + node;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = fr[i];
+    for (int i = 0; i < Q; ++i) g[i] = fr[(long long)i * p.nwall[wf]];
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -591,12 +638,17 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
   } else {
     // Section 3.1: regularized node with the HRFD gradient
     const int yF = yB + s, yFF = yB + 2 * s;
+    // With periodic x every source below is inside the lattice or across a
+    // periodic face (F takes all directions from rows yB..yB+2s, B only those
+    // with c.n >= 0, from rows yB and yF): plain neighbour offsets.
+    const bool px = p.px != 0;
+    const NbOff oF = nb_offsets(p, x, yF, z), oB = nb_offsets(p, x, yB, z);
     R jF[3] = {(R)0.5 * psel<R>(p.F[0], p.F_f[0]), (R)0.5 * psel<R>(p.F[1], p.F_f[1]), (R)0.5 * psel<R>(p.F[2], p.F_f[2])};
     R rhoF = (R)1;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       bool known;
-      const R gi = pull_bc<Q, ST>(p, x, yF, z, i, &known);
+      const R gi = px ? pull_nb<Q, ST>(p, oF, i) : pull_bc<Q, ST>(p, x, yF, z, i, &known);
       rhoF += gi;
       jF[0] += (R)L::c(i, 0) * gi;
       jF[1] += (R)L::c(i, 1) * gi;
@@ -624,22 +676,29 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
       const int cn = -s * L::c(i, 1);   // c . n with n the outward normal
       if (cn >= 0) {
         bool known;
-        const R gi = pull_bc<Q, ST>(p, x, yB, z, i, &known);
+        const R gi = px ? pull_nb<Q, ST>(p, oB, i) : pull_bc<Q, ST>(p, x, yB, z, i, &known);
         if (cn == 0) gpar += gi; else gperp += gi;
       }
     }
     const R rhoB = (R)1 + gpar + (R)2 * gperp;
     // velocity gradient G[a][c] = d_a u_c at B from the previous-step velocity
     R G[3][3];
-    const Nb<R> xm = neighbour<R>(p, vs, x, yB, z, 0, -1);
-    const Nb<R> xp = neighbour<R>(p, vs, x, yB, z, 0, +1);
+    if (px) {
+      const Rec<R> xm = ld_rec(vs, oB.id + oB.oxm), xp = ld_rec(vs, oB.id + oB.oxp);
+      G[0][0] = (R)0.5 * (xp.x - xm.x);
+      G[0][1] = (R)0.5 * (xp.y - xm.y);
+      G[0][2] = (R)0.5 * (xp.z - xm.z);
+    } else {
+      const Nb<R> xm = neighbour<R>(p, vs, x, yB, z, 0, -1);
+      const Nb<R> xp = neighbour<R>(p, vs, x, yB, z, 0, +1);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) G[0][c] = (R)0.5 * (xp.u[c] - xm.u[c]);
+      for (int c = 0; c < 3; ++c) G[0][c] = (R)0.5 * (xp.u[c] - xm.u[c]);
+    }
     if (Q == 19) {
-      const Nb<R> zm = neighbour<R>(p, vs, x, yB, z, 2, -1);
-      const Nb<R> zp = neighbour<R>(p, vs, x, yB, z, 2, +1);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) G[2][c] = (R)0.5 * (zp.u[c] - zm.u[c]);
+      const Rec<R> zm = ld_rec(vs, oB.id + oB.ozm), zp = ld_rec(vs, oB.id + oB.ozp);   // z periodic
+      G[2][0] = (R)0.5 * (zp.x - zm.x);
+      G[2][1] = (R)0.5 * (zp.y - zm.y);
+      G[2][2] = (R)0.5 * (zp.z - zm.z);
     } else {
       G[2][0] = G[2][1] = G[2][2] = (R)0;
     }
@@ -680,14 +739,14 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const R dux = uB[0] - Us;
     const R uu15 = (R)1.5 * (uB[0] * uB[0] + uB[2] * uB[2]);
     const R du15 = (R)1.5 * (dux * ((R)2 * Us + dux) + uB[2] * uB[2]);
-    R* fr = (R*)p.frec[fi] + (long long)node * Q;
+    R* fr = (R*)p.frec[fi] + node;   // [i][node]: the warp's stores coalesce
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
       const R geq = heq_dev<Q, R>(i, rhoB - (R)1, dux, (R)0, uB[2], Us, uu15, du15);
       const R qs = (R)(cx * cx) * Sxx + (R)(cy * cy) * Syy + (R)(cz * cz) * Szz +
                    (R)2 * ((R)(cx * cy) * Sxy + (R)(cx * cz) * Sxz + (R)(cy * cz) * Syz) - trS;
-      fr[i] = geq - (R)3 * (R)L::w(i) * rhoB * tau * qs;     // Eqs. 19, 26
+      fr[(long long)i * p.nwall[fi]] = geq - (R)3 * (R)L::w(i) * rhoB * tau * qs;   // Eqs. 19, 26
     }
     if (p.turbulent) vd[4 * idB + 3] = psel<R>(p.nu, p.nu_f) * (R)WF::kappa * ypB;
   }
@@ -698,13 +757,23 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
   }
 }
 
+// One face per grid row (blockIdx.y); the blocks of a row stride over the
+// face's nodes.  The grid is sized by the host to a few blocks per SM: the
+// pass is bound by the FP64 pipe, which a few warps per SM keep busy, and the
+// registers it does not hold stay with the inner-row kernel running beside it.
+// Minimum resident wall-pass blocks per SM requested from the compiler: its
+// register budget (8: 64 registers), which is also what the pass takes from
+// the inner-row kernel running beside it.
+#ifndef LBM_WALL_MINB
+#define LBM_WALL_MINB 8
+#endif
 template <int Q, int ST>
-__global__ void __launch_bounds__(128) k_wall(const Params p) {
+__global__ void __launch_bounds__(128, LBM_WALL_MINB) k_wall(const Params p) {
   const int fi = blockIdx.y;
   if (!p.wall[fi]) return;
-  const int node = blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= p.nwall[fi]) return;
-  wall_node<Q, ST>(p, fi, node);
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < p.nwall[fi];
+       node += gridDim.x * blockDim.x)
+    wall_node<Q, ST>(p, fi, node);
 }
 
 // ----------------------------------------------------------------------------

@@ -255,8 +255,13 @@ def test_tma_staged_inner_rows(case_fn):
     case = case_fn()
     a = run_gpu(case, 60, tma=True)
     b = run_gpu(case, 60, tma=False)
+    # the direct-load kernel runs the cells of x-periodic BGK rows in pairs on
+    # packed FP32 lanes, without the fused multiply-adds of the scalar code the
+    # staged kernel runs; 16-bit storage turns such last-bit differences into
+    # differences of one storage unit in some populations
+    tol = 1e-6 if case.storage == "fp32" else 1e-4
     for k in ("u", "nu_t"):
-        assert rel(a[k], b[k]) < 1e-6, (case.name, k)
+        assert rel(a[k], b[k]) < tol, (case.name, k)
     if case.storage == "fp32":
         compare(case, 60, TOL["fp32"], tma=True)
 
