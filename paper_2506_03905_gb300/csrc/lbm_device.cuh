@@ -664,22 +664,26 @@ __host__ __device__ inline bool solve_utau(int law, double kap, double B, double
 
 // The same root with the iterations shared between FP32 and FP64.  Newton runs
 // in FP32 from the warm start (the FP32 wall law: logf, atan2f) until its step
-// is below 1e-5 of the iterate, which FP32 resolves; one Newton step in FP64
-// with the exact FP64 wall law then completes the inversion (quadratic
-// convergence: the FP32 iterate is within ~1e-6 of the root, the FP64 step
-// leaves ~1e-12).  A developing flow, whose u_tau moves by more than 1e-5 per
-// step, thereby costs one FP64 evaluation of Eq. 16 per node and step instead
-// of two; on GB300 the FP64 logarithms and arctangents run at 1/64 of the FP32
-// rate.  Falls back to the FP64 iteration (solve_utau) if the FP32 one does not
-// settle or the FP64 step is not small.
+// is below 1e-5 of the iterate, which FP32 resolves; one Newton step on the
+// exact FP64 residual (Eq. 16 in FP64) then completes the inversion.  That
+// step's slope is the FP32 one of the last iteration: it is needed only to
+// ~1e-5 relative for a correction of ~1e-6 of u_tau, which leaves ~1e-11.  A
+// developing flow, whose u_tau moves by more than 1e-5 per step, thereby costs
+// one FP64 evaluation of the wall law per node and step instead of two or
+// three with their slopes and divisions; on GB300 the FP64 logarithms and
+// arctangents run at 1/64 of the FP32 rate.  Falls back to the FP64 iteration
+// (solve_utau) if the FP32 one does not settle or the FP64 step is not small.
+// inv_nu = 1 / nu.
 __device__ inline bool solve_utau_mixed(int law, double kap, double B, double U, double y,
-                                        double nu, double guess, double* out) {
+                                        double nu, double inv_nu, double guess, double* out) {
   if (!(U > 0.0)) {
     *out = 0.0;
     return true;
   }
-  const float Uf = (float)U, yn = (float)(y / nu), kf = (float)kap, Bf = (float)B;
+  const double ynd = y * inv_nu;   // y / nu
+  const float Uf = (float)U, yn = (float)ynd, kf = (float)kap, Bf = (float)B;
   float xf = guess > 0.0 ? (float)guess : sqrtf(Uf / yn);
+  float dgf = 1.0f;
   bool settled = false;
   for (int it = 0; it < 8; ++it) {
     const float yp = xf * yn;
@@ -689,6 +693,7 @@ __device__ inline bool solve_utau_mixed(int law, double kap, double B, double U,
     const float xn = xf - step;
     if (!(dg > 0.0f) || !(xn > 0.0f)) break;
     xf = xn;
+    dgf = dg;
     if (fabsf(step) <= 1e-5f * xf) {
       settled = true;
       break;
@@ -696,12 +701,9 @@ __device__ inline bool solve_utau_mixed(int law, double kap, double B, double U,
   }
   const double x = settled ? (double)xf : guess;
   if (settled) {
-    const double yp = x * y / nu;
-    const double up = wf_uplus(law, kap, B, yp);
-    const double dg = up + yp * wf_dudy(law, kap, yp);
-    const double step = (x * up - U) / dg;
+    const double step = (x * wf_uplus(law, kap, B, x * ynd) - U) * (double)__fdividef(1.0f, dgf);
     const double xn = x - step;
-    if (dg > 0.0 && fabs(step) <= 1e-4 * x && xn > 0.0) {
+    if (fabs(step) <= 1e-4 * x && xn > 0.0) {
       *out = xn;
       return true;
     }

@@ -618,8 +618,8 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     R* uw = (R*)p.uw[fi] + 3 * node;
     if (!isfinite(Um)) atomicOr(p.flags, FLAG_NONFINITE);   // reported, not turned into u_tau = 0
     if (p.turbulent) {
-      ok = solve_utau_mixed(p.wall_law, p.law_kappa, p.law_B, (double)Um, yref, nu, p.utau[fi][node],
-                            &ut);
+      ok = solve_utau_mixed(p.wall_law, p.law_kappa, p.law_B, (double)Um, yref, nu, p.inv_nu,
+                            p.utau[fi][node], &ut);
       const R utr = (R)ut, nur = psel<R>(p.nu, p.nu_f), kap = (R)WF::kappa;
       const R ypB = utr * (R)dw * psel<R>(p.inv_nu, p.inv_nu_f);
       // Eq. 35 with Delta_w = y_B = d_w and nu_t|_B = nu kappa y_B+
@@ -663,8 +663,8 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const double dw = p.d_w[fi];                       // y_B; y_F = 1 + d_w
     if (!isfinite(Um)) atomicOr(p.flags, FLAG_NONFINITE);
     if (p.turbulent)
-      ok = solve_utau_mixed(p.wall_law, p.law_kappa, p.law_B, (double)Um, 1.0 + dw, nu, p.utau[fi][node],
-                      &ut);
+      ok = solve_utau_mixed(p.wall_law, p.law_kappa, p.law_B, (double)Um, 1.0 + dw, nu, p.inv_nu,
+                            p.utau[fi][node], &ut);
     const R utr = (R)ut, inu = psel<R>(p.inv_nu, p.inv_nu_f);
     const R ypB = utr * (R)dw * inu;
     const R upB = p.turbulent ? utr * wf_uplus_r<R>(p, ypB) : (R)0;   // u_B = u_tau u+(y_B+)
@@ -740,13 +740,25 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const R uu15 = (R)1.5 * (uB[0] * uB[0] + uB[2] * uB[2]);
     const R du15 = (R)1.5 * (dux * ((R)2 * Us + dux) + uB[2] * uB[2]);
     R* fr = (R*)p.frec[fi] + node;   // [i][node]: the warp's stores coalesce
+    const long long nw = p.nwall[fi];
+    // Eqs. 19, 26: f_i = f_i^eq(rho_B, u_B) - 3 w_i rho_B tau Q_i:S, over opposite
+    // pairs (i, i+1): Q_i:S is even in c_i, the equilibrium splits into the even
+    // and odd parts of the per-weight-class polynomial (eq_pair)
+    const R drB = rhoB - (R)1, one_m_uu15 = (R)1 - uu15, rt3 = (R)3 * rhoB * tau;
+    const EqCoef<R> k1 = eq_coef<R>((R)L::w(1), rhoB, drB, Us, one_m_uu15, du15);
+    const EqCoef<R> k2 = eq_coef<R>((R)L::w(Q == 19 ? 7 : 5), rhoB, drB, Us, one_m_uu15, du15);
+    fr[0] = (R)L::w(0) * ((drB * one_m_uu15 - du15) + rt3 * trS);   // Q_0:S = -tr(S)/3
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; i += 2) {
       const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-      const R geq = heq_dev<Q, R>(i, rhoB - (R)1, dux, (R)0, uB[2], Us, uu15, du15);
+      const EqCoef<R>& k = L::w(i) < L::w(1) ? k2 : k1;
+      R ev, od;
+      eq_pair<Q, R>(k, cx, cdot<Q, R>(i, dux, (R)0, uB[2]), &ev, &od);
       const R qs = (R)(cx * cx) * Sxx + (R)(cy * cy) * Syy + (R)(cz * cz) * Szz +
                    (R)2 * ((R)(cx * cy) * Sxy + (R)(cx * cz) * Sxz + (R)(cy * cz) * Syz) - trS;
-      fr[(long long)i * p.nwall[fi]] = geq - (R)3 * (R)L::w(i) * rhoB * tau * qs;   // Eqs. 19, 26
+      const R e = ev - (R)L::w(i) * rt3 * qs;
+      fr[i * nw] = e + od;
+      fr[(i + 1) * nw] = e - od;
     }
     if (p.turbulent) vd[4 * idB + 3] = psel<R>(p.nu, p.nu_f) * (R)WF::kappa * ypB;
   }
