@@ -189,10 +189,13 @@ lbm_status lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* u,
    that synchronises (lbm_fields, lbm_diagnostics). */
 lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
 
-/* Same steps launched without a graph, with CUDA events around every kernel;
-   kernel_ms[0] receives the total time of the bulk kernel, kernel_ms[1] of
-   the wall pre-pass kernel, summed over the nsteps (synchronises). */
-lbm_status lbm_step_timed(lbm_ctx* ctx, int nsteps, float kernel_ms[2]);
+/* Same steps launched without a graph, one kernel after the other, with CUDA
+   events around them; summed over the nsteps: kernel_ms[0] the bulk rows
+   (inner rows, then wall rows; every row of a lattice without walls),
+   kernel_ms[1] the wall pre-pass, kernel_ms[2] the inner rows alone (the
+   face-free kernel; equal to kernel_ms[0] without walls).  Synchronises
+   cfg.stream.  Bookkeeping for benchmarks: the paper has no counterpart. */
+lbm_status lbm_step_timed(lbm_ctx* ctx, int nsteps, float kernel_ms[3]);
 
 /* Copy the fields selected by mask (LBM_FIELD_*) into caller buffers dst[k]
    (float64, physical units), in increasing bit order: rho = sum f_i (Eq. 4) and

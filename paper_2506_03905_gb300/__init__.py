@@ -169,9 +169,10 @@ def lbm_step(ctx, nsteps: int):
 
 
 def lbm_step_timed(ctx, nsteps: int):
-    ms = (ctypes.c_float * 2)()
+    """(bulk rows, wall pre-pass, inner rows) kernel milliseconds over nsteps."""
+    ms = (ctypes.c_float * 3)()
     _check(lib().lbm_step_timed(ctx, int(nsteps), ms), "lbm_step_timed", ctx)
-    return float(ms[0]), float(ms[1])
+    return float(ms[0]), float(ms[1]), float(ms[2])
 
 
 def lbm_fields(ctx, mask: int, ptrs: Sequence[int], on_device: bool):
@@ -386,6 +387,11 @@ class Solver:
         lbm_step(self.ctx, n)
 
     def step_timed(self, n: int):
+        """(bulk rows, wall pre-pass) kernel milliseconds over n steps."""
+        return lbm_step_timed(self.ctx, n)[:2]
+
+    def step_timed3(self, n: int):
+        """(bulk rows, wall pre-pass, inner rows) kernel milliseconds over n steps."""
         return lbm_step_timed(self.ctx, n)
 
     def fields(self, names: Sequence[str] = ("rho", "u", "nu_t", "nu_tilde"),

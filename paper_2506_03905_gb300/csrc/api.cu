@@ -219,8 +219,7 @@ extern "C" lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     c->utau[b] = (double*)dalloc(c, nodes * sizeof(double));
     c->uw[b] = dalloc(c, 3 * nodes * c->rsz);
     c->rhow[b] = dalloc(c, nodes * c->rsz);
-    c->frec[b] = dalloc(c, (size_t)c->Q * nodes * c->rsz);
-    ok = ok && c->f[b] && c->v[b] && c->utau[b] && c->uw[b] && c->rhow[b] && c->frec[b];
+    ok = ok && c->f[b] && c->v[b] && c->utau[b] && c->uw[b] && c->rhow[b];
   }
   c->utau_prev = (double*)dalloc(c, 2 * (size_t)k.nx * k.nz * sizeof(double));
   c->invd2 = dalloc(c, (size_t)c->pitch * k.ny * c->rsz);
@@ -422,7 +421,6 @@ lbm_status lbm_ctx_finalize(lbm_ctx* c) {
     p.utau[b] = c->utau[b];
     p.uw[b] = c->uw[b];
     p.rhow[b] = c->rhow[b];
-    p.frec[b] = c->frec[b];
   }
   p.flags = c->flags;
   p.wait_limit = c->wait_limit;
@@ -627,6 +625,15 @@ static void launch_all_rows(lbm_ctx* c, const Params& p, cudaStream_t s) {
   launch_bulk(c, p, ROWS_WALL, s);
 }
 
+// Whether the wall rows hold cells the wall pass does not step itself (it steps
+// regularized wall nodes): bounce-back nodes, a face without a wall, or the
+// columns upstream of a wall's leading edge.
+static bool wall_rows_needed(const Params& p) {
+  for (int f = 0; f < 2; ++f)
+    if (!(p.wall[f] && p.wall[f] != BC_WALL_BB && p.xw0[f] == 0)) return true;
+  return false;
+}
+
 // One step.  With walls, only the two wall rows depend on the wall pre-pass:
 // the inner rows run on `s` while the side stream runs the wall pre-pass and
 // then the wall rows (fork / join through events, also inside graph capture).
@@ -639,7 +646,7 @@ static void launch_step(lbm_ctx* c, int src, cudaStream_t s) {
   cudaEventRecord(c->ev_fork, s);
   cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
   launch_wall(c, p, c->side_stream, c->prio_hi);
-  launch_bulk(c, p, ROWS_WALL, c->side_stream, c->prio_hi);
+  if (wall_rows_needed(p)) launch_bulk(c, p, ROWS_WALL, c->side_stream, c->prio_hi);
   cudaEventRecord(c->ev_join, c->side_stream);
   launch_bulk(c, p, ROWS_INNER, s);
   cudaStreamWaitEvent(s, c->ev_join, 0);
@@ -764,7 +771,7 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, int nsteps) {
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int nsteps, float kernel_ms[2]) {
+extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int nsteps, float kernel_ms[3]) {
   if (!c || nsteps < 0 || !kernel_ms) return LBM_EINVAL;
   if (!c->ready) {
     lbm_ctx_set_error(c, "lbm_set_fields (or lbm_set_state) must come first");
@@ -772,38 +779,45 @@ extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int nsteps, float kernel_ms[2])
   }
   lbm_status s = lbm_ctx_finalize(c);
   if (s != LBM_OK) return s;
-  std::vector<cudaEvent_t> ev(3 * (size_t)nsteps);
+  std::vector<cudaEvent_t> ev(4 * (size_t)nsteps);
   for (auto& e : ev) CUDA_TRY(c, cudaEventCreate(&e));
   for (int k = 0; k < nsteps; ++k) {
     // the kernels of lbm_step, one after the other so that each one's duration
     // is measurable: wall pre-pass, then bulk (inner rows, then wall rows)
     const Params p = lbm_ctx_params(c, c->cur);
     const bool walls = p.wall[0] || p.wall[1];
-    CUDA_TRY(c, cudaEventRecord(ev[3 * k], c->stream));
+    cudaEvent_t* e = &ev[4 * (size_t)k];
+    CUDA_TRY(c, cudaEventRecord(e[0], c->stream));
     if (walls) launch_wall(c, p, c->stream);
-    CUDA_TRY(c, cudaEventRecord(ev[3 * k + 1], c->stream));
+    CUDA_TRY(c, cudaEventRecord(e[1], c->stream));
     if (walls) {
       launch_bulk(c, p, ROWS_INNER, c->stream);
-      launch_bulk(c, p, ROWS_WALL, c->stream);
+      CUDA_TRY(c, cudaEventRecord(e[2], c->stream));
+      if (wall_rows_needed(p)) launch_bulk(c, p, ROWS_WALL, c->stream);
     } else {
       launch_all_rows(c, p, c->stream);
+      CUDA_TRY(c, cudaEventRecord(e[2], c->stream));
     }
-    CUDA_TRY(c, cudaEventRecord(ev[3 * k + 2], c->stream));
+    CUDA_TRY(c, cudaEventRecord(e[3], c->stream));
     c->cur ^= 1;
   }
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  float wall = 0.f, bulk = 0.f;
+  float wall = 0.f, bulk = 0.f, inner = 0.f;
   for (int k = 0; k < nsteps; ++k) {
-    float a = 0.f, b = 0.f;
-    cudaEventElapsedTime(&a, ev[3 * k], ev[3 * k + 1]);
-    cudaEventElapsedTime(&b, ev[3 * k + 1], ev[3 * k + 2]);
+    const cudaEvent_t* e = &ev[4 * (size_t)k];
+    float a = 0.f, b = 0.f, d = 0.f;
+    cudaEventElapsedTime(&a, e[0], e[1]);
+    cudaEventElapsedTime(&b, e[1], e[3]);
+    cudaEventElapsedTime(&d, e[1], e[2]);
     wall += a;
     bulk += b;
+    inner += d;
   }
   for (auto& e : ev) cudaEventDestroy(e);
   kernel_ms[0] = bulk;
   kernel_ms[1] = wall;
+  kernel_ms[2] = inner;
   c->steps_done += nsteps;
   return LBM_OK;
 }

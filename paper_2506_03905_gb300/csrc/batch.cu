@@ -91,14 +91,27 @@ constexpr long long kSpinLimit = 1LL << 24;   // x ~64 ns sleep: about one secon
 // Lane 0 waits until *ctr >= target; false if the wait gave up or another warp
 // already failed.  spin_limit == 0 is the test setting: every wait that would
 // have to poll at all gives up at once.
+// Counter reads and increments with acquire / release semantics at GPU scope
+// (instead of full fences around plain accesses).  The warp's other lanes are
+// ordered with lane 0's accesses by __syncwarp.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned add_release(unsigned* p, unsigned a) {
+  unsigned old;
+  asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(a) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target, BatchCtl* ctl,
                                            long long spin_limit, int lane) {
   int ok = 1;
   if (lane == 0 && target > 0) {
-    volatile const unsigned* v = ctr;
     volatile const unsigned* verr = &ctl->err;
     long long it = 0;
-    while (*v < target) {
+    while (ld_acquire(ctr) < target) {   // acquire: the producers' writes are visible after it
       if (*verr) {
         ok = 0;
         break;
@@ -110,7 +123,6 @@ __device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target,
       }
       __nanosleep(64);
     }
-    __threadfence();   // acquire: the producers' writes are visible after this
   }
   ok = __shfl_sync(0xffffffffu, ok, 0);
   __syncwarp();
@@ -205,9 +217,9 @@ __global__ void LBM_BATCH_BOUNDS k_batch(BatchInst* inst, const WorkItem* items,
     }
     __syncwarp();
     if (lane == 0) {
-      __threadfence();   // release: this item's writes before its count
-      if (w.kind == KIND_A) atomicAdd(&done_a[w.inst], 1u);
-      const unsigned d = atomicAdd(&done[w.inst], 1u) + 1u;
+      // release: this item's writes (all lanes, ordered by the __syncwarp) before its count
+      if (w.kind == KIND_A) add_release(&done_a[w.inst], 1u);
+      const unsigned d = add_release(&done[w.inst], 1u) + 1u;
       // the instance's last item of this launch: no other item of it remains
       if (d == (unsigned)nsteps * per) b.cur = (b.cur + nsteps) & 1;
     }

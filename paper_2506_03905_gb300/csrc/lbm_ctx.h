@@ -30,7 +30,6 @@ struct lbm_ctx {
   double* utau[2] = {nullptr, nullptr};
   void* uw[2] = {nullptr, nullptr};
   void* rhow[2] = {nullptr, nullptr};
-  void* frec[2] = {nullptr, nullptr};
   void* invd2 = nullptr;   // 1 / d^2 of the SA model per (y, x), compute type, [y * pitch + x]
   double* utau_prev = nullptr;
   unsigned* flags = nullptr;

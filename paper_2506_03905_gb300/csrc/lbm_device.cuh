@@ -302,7 +302,6 @@ struct Params {
   double* utau[2];             // per wall node, FP64 (also the Newton warm start)
   void* uw[2];                 // BB: slip velocity (3 per node), compute type
   void* rhow[2];               // BB: wall density, compute type
-  void* frec[2];               // HRFD: rebuilt populations [i][node], deviations, compute type
   const void* invd2;           // 1 / d^2 (wall distance of the SA model), compute type, [y][x]
   unsigned* flags;
   long long wait_limit;        // polls of a bounded device-side wait before it gives up

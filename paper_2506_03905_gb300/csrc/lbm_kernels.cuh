@@ -111,8 +111,10 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
 // even, both with in-lattice or periodic neighbours, in one thread: the
 // populations of the directions with c_x = 0 are read for both cells with one
 // paired access, every post-collision pair is written with one, the SA stencil
-// reads 12 records for both cells instead of 14, and the index arithmetic is
-// shared.  Each cell computes exactly what bulk_interior computes.
+// reads 12 records for both cells instead of 14, the index arithmetic is
+// shared, and the FP32 arithmetic runs on packed lanes (f2).  Each cell follows
+// the steps of bulk_interior; the packed lanes round products and sums
+// separately where the scalar code may fuse them.
 template <int Q, int ST>
 __device__ __forceinline__ void bulk_interior2(const Params& p, int x0, int y, int z) {
   using L = Lat<Q>;
@@ -322,6 +324,7 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
   int wf = -1;
   if (y == 0 && p.wall[0] && x >= p.xw0[0]) wf = 0;
   else if (y == p.ny - 1 && p.wall[1] && x >= p.xw0[1]) wf = 1;
+  if (wf >= 0 && p.wall[wf] != BC_WALL_BB) return;   // regularized wall node: done by the wall pass
   const bool inlet = (x == 0 && p.kind[XMIN] == BC_INLET);
 
   // 1. SA working variable of the new step (Dirichlet at wall nodes and inlet)
@@ -339,47 +342,40 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
   const R nut = p.turbulent ? sa_nut<R>(ntn, psel<R>(p.inv_nu, p.inv_nu_f)) : (R)0;
   const R delta = relax_delta<R>((R)3 * (nu + nut));   // 2 - omega (Eq. 8)
 
-  // 2. post-stream populations
+  // 2. post-stream populations (regularized wall nodes are rebuilt by the wall pass)
   R g[Q];
-  if (wf >= 0 && p.wall[wf] != BC_WALL_BB) {   // regularized wall: rebuilt populations
-    const int node = z * (p.nx - p.xw0[wf]) + (x - p.xw0[wf]);
-    const R* fr = (const R*)p.frec[wf] + node;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = fr[(long long)i * p.nwall[wf]];
-  } else {
+  for (int i = 0; i < Q; ++i) {
+    bool known;
+    g[i] = pull_bc<Q, ST>(p, x, y, z, i, &known);
+  }
+  if (inlet) {
+    // Zou-He velocity inlet: unknowns c_x > 0 from the non-equilibrium
+    // bounce-back of the normal direction plus transverse corrections.
+    const R ux = psel<R>(p.u_face[XMIN][0], p.u_face_f[XMIN][0]), uy = psel<R>(p.u_face[XMIN][1], p.u_face_f[XMIN][1]), uz = psel<R>(p.u_face[XMIN][2], p.u_face_f[XMIN][2]);
+    R s0 = 0, sm = 0, ky = 0, kz = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      bool known;
-      g[i] = pull_bc<Q, ST>(p, x, y, z, i, &known);
-    }
-    if (inlet) {
-      // Zou-He velocity inlet: unknowns c_x > 0 from the non-equilibrium
-      // bounce-back of the normal direction plus transverse corrections.
-      const R ux = psel<R>(p.u_face[XMIN][0], p.u_face_f[XMIN][0]), uy = psel<R>(p.u_face[XMIN][1], p.u_face_f[XMIN][1]), uz = psel<R>(p.u_face[XMIN][2], p.u_face_f[XMIN][2]);
-      R s0 = 0, sm = 0, ky = 0, kz = 0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (L::c(i, 0) == 0) {
-          s0 += g[i];
-          ky += (R)L::c(i, 1) * g[i];
-          kz += (R)L::c(i, 2) * g[i];
-        } else if (L::c(i, 0) < 0) {
-          sm += g[i];
-        }
+      if (L::c(i, 0) == 0) {
+        s0 += g[i];
+        ky += (R)L::c(i, 1) * g[i];
+        kz += (R)L::c(i, 2) * g[i];
+      } else if (L::c(i, 0) < 0) {
+        sm += g[i];
       }
-      // in deviations from E = f^eq(1, U x): sum_{cx=0} E + 2 sum_{cx<0} E = 1 - U and
-      // E_{opp i} - E_i = -6 w c_x U
-      const R U = psel<R>(p.Ush, p.Ush_f);
-      const R rho = fdiv(((R)1 - U) + s0 + (R)2 * sm, (R)1 - ux);
-      const R Ny = (R)0.5 * ky - rho * uy * (R)(1.0 / 3.0);
-      const R Nz = (R)0.5 * kz - rho * uz * (R)(1.0 / 3.0);
+    }
+    // in deviations from E = f^eq(1, U x): sum_{cx=0} E + 2 sum_{cx<0} E = 1 - U and
+    // E_{opp i} - E_i = -6 w c_x U
+    const R U = psel<R>(p.Ush, p.Ush_f);
+    const R rho = fdiv(((R)1 - U) + s0 + (R)2 * sm, (R)1 - ux);
+    const R Ny = (R)0.5 * ky - rho * uy * (R)(1.0 / 3.0);
+    const R Nz = (R)0.5 * kz - rho * uz * (R)(1.0 / 3.0);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (L::c(i, 0) > 0) {
-          const R cu = (R)L::c(i, 0) * ux + (R)L::c(i, 1) * uy + (R)L::c(i, 2) * uz;
-          g[i] = g[opp(i)] + (R)6 * (R)L::w(i) * (rho * cu - (R)L::c(i, 0) * U) -
-                 (R)L::c(i, 1) * Ny - (R)L::c(i, 2) * Nz;
-        }
+    for (int i = 0; i < Q; ++i) {
+      if (L::c(i, 0) > 0) {
+        const R cu = (R)L::c(i, 0) * ux + (R)L::c(i, 1) * uy + (R)L::c(i, 2) * uz;
+        g[i] = g[opp(i)] + (R)6 * (R)L::w(i) * (rho * cu - (R)L::c(i, 0) * U) -
+               (R)L::c(i, 1) * Ny - (R)L::c(i, 2) * Nz;
       }
     }
   }
@@ -739,15 +735,14 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const R dux = uB[0] - Us;
     const R uu15 = (R)1.5 * (uB[0] * uB[0] + uB[2] * uB[2]);
     const R du15 = (R)1.5 * (dux * ((R)2 * Us + dux) + uB[2] * uB[2]);
-    R* fr = (R*)p.frec[fi] + node;   // [i][node]: the warp's stores coalesce
-    const long long nw = p.nwall[fi];
     // Eqs. 19, 26: f_i = f_i^eq(rho_B, u_B) - 3 w_i rho_B tau Q_i:S, over opposite
     // pairs (i, i+1): Q_i:S is even in c_i, the equilibrium splits into the even
     // and odd parts of the per-weight-class polynomial (eq_pair)
+    R g[Q];
     const R drB = rhoB - (R)1, one_m_uu15 = (R)1 - uu15, rt3 = (R)3 * rhoB * tau;
     const EqCoef<R> k1 = eq_coef<R>((R)L::w(1), rhoB, drB, Us, one_m_uu15, du15);
     const EqCoef<R> k2 = eq_coef<R>((R)L::w(Q == 19 ? 7 : 5), rhoB, drB, Us, one_m_uu15, du15);
-    fr[0] = (R)L::w(0) * ((drB * one_m_uu15 - du15) + rt3 * trS);   // Q_0:S = -tr(S)/3
+    g[0] = (R)L::w(0) * ((drB * one_m_uu15 - du15) + rt3 * trS);   // Q_0:S = -tr(S)/3
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
       const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
@@ -757,10 +752,20 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
       const R qs = (R)(cx * cx) * Sxx + (R)(cy * cy) * Syy + (R)(cz * cz) * Szz +
                    (R)2 * ((R)(cx * cy) * Sxy + (R)(cx * cz) * Sxz + (R)(cy * cz) * Syz) - trS;
       const R e = ev - (R)L::w(i) * rt3 * qs;
-      fr[i * nw] = e + od;
-      fr[(i + 1) * nw] = e - od;
+      g[i] = e + od;
+      g[i + 1] = e - od;
     }
-    if (p.turbulent) vd[4 * idB + 3] = psel<R>(p.nu, p.nu_f) * (R)WF::kappa * ypB;
+    // the node's own step, in the wall pass: nu_tilde_B (Dirichlet), relaxation
+    // rate, collision of the rebuilt populations and the stores (the wall-row
+    // kernels leave regularized wall nodes alone)
+    const R ntn = p.turbulent ? psel<R>(p.nu, p.nu_f) * (R)WF::kappa * ypB : ntB;
+    const R nutn = p.turbulent ? sa_nut<R>(ntn, psel<R>(p.inv_nu, p.inv_nu_f)) : (R)0;
+    R u[3];
+    collide<Q, R>(p, g, relax_delta<R>((R)3 * (psel<R>(p.nu, p.nu_f) + nutn)), u);   // Eq. 8
+    T* LBM_RESTRICT fdst = (T*)p.f_dst;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) C::st(fdst + i * p.ncell + idB, g[i]);
+    st_rec(vd, idB, u[0], u[1], u[2], ntn);
   }
   p.utau[fi][node] = ut;
   if (!ok) {   // Newton reached its iteration limit: flag and count the node update
