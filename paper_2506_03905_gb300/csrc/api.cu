@@ -583,16 +583,25 @@ void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b) {
 #define LBM_WALL_BLOCKS_PER_SM 2
 #endif
 
+// One launch per wall class present (bounce-back, regularized): each kernel
+// holds one scheme's code and leaves the other class's face alone.
 static void launch_wall(lbm_ctx* c, const Params& p, cudaStream_t s, int prio = 0) {
-  const int maxw = std::max(p.wall[0] ? p.nwall[0] : 0, p.wall[1] ? p.nwall[1] : 0);
-  const int faces = (p.wall[0] ? 1 : 0) + (p.wall[1] ? 1 : 0);
-  const bool regularized = (p.wall[0] && p.wall[0] != BC_WALL_BB) || (p.wall[1] && p.wall[1] != BC_WALL_BB);
-  int gx = (maxw + 127) / 128;
-  if (!regularized) gx = std::min(gx, std::max(1, c->sms * LBM_WALL_BLOCKS_PER_SM / std::max(faces, 1)));
-  dim3 g(gx, 2, 1), b(128, 1, 1);
-  if (c->Q == 9) launch_wall_q9(c->st, p, g, b, s, prio);
-  else launch_wall_q19(c->st, p, g, b, s, prio);
-  ++c->launches;
+  for (int cls = 0; cls < 2; ++cls) {
+    const bool regularized = cls == 1;
+    int maxw = 0, faces = 0;
+    for (int f = 0; f < 2; ++f)
+      if (p.wall[f] && (p.wall[f] != BC_WALL_BB) == regularized) {
+        maxw = std::max(maxw, p.nwall[f]);
+        ++faces;
+      }
+    if (faces == 0) continue;
+    int gx = (maxw + 127) / 128;
+    if (!regularized) gx = std::min(gx, std::max(1, c->sms * LBM_WALL_BLOCKS_PER_SM / faces));
+    dim3 g(gx, 2, 1), b(128, 1, 1);
+    if (c->Q == 9) launch_wall_q9(c->st, p, regularized, g, b, s, prio);
+    else launch_wall_q19(c->st, p, regularized, g, b, s, prio);
+    ++c->launches;
+  }
 }
 
 static void launch_bulk(lbm_ctx* c, const Params& p, int rows, cudaStream_t s, int prio = 0) {

@@ -69,8 +69,9 @@ static void bulk_st(const Params& p, int rows, bool pairs, dim3 g, dim3 b, cudaS
   else launch_prio(k_bulk<LBM_Q, ST, true>, g, b, s, prio, p, rows);
 }
 template <int ST>
-static void wall_st(const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
-  launch_prio(k_wall<LBM_Q, ST>, g, b, s, prio, p);
+static void wall_st(const Params& p, bool regularized, dim3 g, dim3 b, cudaStream_t s, int prio) {
+  if (regularized) launch_prio(k_wall<LBM_Q, ST, WALLS_REG>, g, b, s, prio, p);
+  else launch_prio(k_wall<LBM_Q, ST, WALLS_BB>, g, b, s, prio, p);
 }
 
 #define LBM_DISPATCH(FN, ...)                       \
@@ -88,8 +89,9 @@ void LBM_QNAME(launch_bulk)(int st, const Params& p, int rows, bool pairs, dim3 
 void LBM_QNAME(launch_bulk_tma)(int st, const Params& p, const CUtensorMap& tm, int zchunk, cudaStream_t s) {
   LBM_DISPATCH(bulk_tma_st, p, tm, zchunk, s)
 }
-void LBM_QNAME(launch_wall)(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio) {
-  LBM_DISPATCH(wall_st, p, g, b, s, prio)
+void LBM_QNAME(launch_wall)(int st, const Params& p, bool regularized, dim3 g, dim3 b, cudaStream_t s,
+                           int prio) {
+  LBM_DISPATCH(wall_st, p, regularized, g, b, s, prio)
 }
 
 template <int ST>

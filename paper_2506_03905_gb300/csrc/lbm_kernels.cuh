@@ -581,7 +581,11 @@ __global__ void __launch_bounds__(256, LBM_TMA_MINB)
 // ----------------------------------------------------------------------------
 // Wall pre-pass: one thread per wall node of face fi (0 = ymin, 1 = ymax).
 // ----------------------------------------------------------------------------
-template <int Q, int ST>
+// WALLS: the wall class the caller has checked (WALLS_BB: slip bounce-back,
+// WALLS_REG: regularized, HRFD or Cai-Degrigny), whose branch alone is compiled;
+// WALLS_ANY decides per face at run time.
+enum { WALLS_ANY = 0, WALLS_BB = 1, WALLS_REG = 2 };
+template <int Q, int ST, int WALLS = WALLS_ANY>
 __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
   using L = Lat<Q>;
   using C = Codec<ST>;
@@ -600,7 +604,8 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
   double ut = 0.0;
   bool ok = true;
 
-  if (p.wall[fi] == BC_WALL_BB) {
+  const bool bb = WALLS == WALLS_BB || (WALLS == WALLS_ANY && p.wall[fi] == BC_WALL_BB);
+  if (bb) {
     // Section 3.2: u_tau from the tangential velocity at the reference node.
     // Everything but the Newton inversion runs in the compute type R.
     const int yR = yB + s * (p.ref_node[fi] - 1);
@@ -784,13 +789,19 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
 #ifndef LBM_WALL_MINB
 #define LBM_WALL_MINB 8
 #endif
-template <int Q, int ST>
-__global__ void __launch_bounds__(128, LBM_WALL_MINB) k_wall(const Params p) {
+#ifndef LBM_WALL_REG_MINB
+#define LBM_WALL_REG_MINB LBM_WALL_MINB   // the regularized class's budget
+#endif
+// One kernel per wall class (WALLS_BB / WALLS_REG), so that a warp's code holds
+// one scheme only; a face of the other class is left to the other kernel.
+template <int Q, int ST, int WALLS>
+__global__ void __launch_bounds__(128, WALLS == WALLS_BB ? LBM_WALL_MINB : LBM_WALL_REG_MINB)
+    k_wall(const Params p) {
   const int fi = blockIdx.y;
-  if (!p.wall[fi]) return;
+  if (!p.wall[fi] || (p.wall[fi] == BC_WALL_BB) != (WALLS == WALLS_BB)) return;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < p.nwall[fi];
        node += gridDim.x * blockDim.x)
-    wall_node<Q, ST>(p, fi, node);
+    wall_node<Q, ST, WALLS>(p, fi, node);
 }
 
 // ----------------------------------------------------------------------------

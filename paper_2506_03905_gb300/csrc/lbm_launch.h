@@ -8,7 +8,8 @@ namespace lbm {
 #define LBM_DECLARE_LAUNCHERS(Q)                                                               \
   void launch_bulk_q##Q(int st, const Params& p, int rows, bool pairs, dim3 g, dim3 b,         \
                         cudaStream_t s, int prio);                                             \
-  void launch_wall_q##Q(int st, const Params& p, dim3 g, dim3 b, cudaStream_t s, int prio);    \
+  void launch_wall_q##Q(int st, const Params& p, bool regularized, dim3 g, dim3 b,              \
+                        cudaStream_t s, int prio);                                             \
   void launch_bulk_tma_q##Q(int st, const Params& p, const CUtensorMap& tm, int zchunk,        \
                             cudaStream_t s);                                                   \
   void launch_init_q##Q(int st, const Params& p, int grid, const double* rho, const double* u, \
