@@ -147,10 +147,13 @@ __device__ __forceinline__ void warp_load_params(Params* dst, const Params* src,
 }
 
 // Minimum resident blocks per SM requested from the compiler for k_batch (its
-// register budget; 0 leaves the choice to the compiler).  Three blocks of 256
-// (<= 80 registers) measured fastest on GB300 for the 96-instance sweep.
+// register budget; 0 leaves the choice to the compiler).  Two blocks of 256
+// (<= 128 registers) measured fastest on GB300 for the 96-instance sweep
+// (FP32 21.1k MLUPS; 3 blocks / 80 registers 19.8k, 4 / 64 17.1k, 1 / 208
+// 21.0k, the compiler's choice 20.0k).  Two cells per lane iteration with both
+// cells' loads issued first measured slower (19.5k).
 #ifndef LBM_BATCH_MINB
-#define LBM_BATCH_MINB 3
+#define LBM_BATCH_MINB 2
 #endif
 #if LBM_BATCH_MINB > 0
 #define LBM_BATCH_BOUNDS __launch_bounds__(256, LBM_BATCH_MINB)
@@ -158,15 +161,36 @@ __device__ __forceinline__ void warp_load_params(Params* dst, const Params* src,
 #define LBM_BATCH_BOUNDS __launch_bounds__(256)
 #endif
 
-// Cell (x, y, z) of entry c of a cell item's box.
-__device__ __forceinline__ void item_cell(const WorkItem& w, int c, int* x, int* y, int* z) {
-  const int per_z = w.ncol * w.nrow;
-  *z = c / per_z;
-  const int r = c - *z * per_z;
-  const int j = r / w.ncol;
-  *x = w.xa + (r - j * w.ncol) * w.xs;
-  *y = w.ya + j * w.ys;
-}
+// The entries c0, c0 + 32, c0 + 64, ... of a cell item's box (ncol columns of
+// stride xs from xa, nrow rows of stride ys from ya, then planes) as cell
+// coordinates: one division set for the first entry, then carries.
+struct BoxWalk {
+  int col, row, z;
+  int dcol, drow;   // 32 entries = drow rows and dcol columns
+  __device__ __forceinline__ BoxWalk(const WorkItem& w, int c0) {
+    const int per_z = w.ncol * w.nrow;
+    z = c0 / per_z;
+    const int r = c0 - z * per_z;
+    row = r / w.ncol;
+    col = r - row * w.ncol;
+    drow = 32 / w.ncol;
+    dcol = 32 - drow * w.ncol;
+  }
+  __device__ __forceinline__ int x(const WorkItem& w) const { return w.xa + col * w.xs; }
+  __device__ __forceinline__ int y(const WorkItem& w) const { return w.ya + row * w.ys; }
+  __device__ __forceinline__ void next(const WorkItem& w) {
+    col += dcol;
+    if (col >= w.ncol) {
+      col -= w.ncol;
+      ++row;
+    }
+    row += drow;
+    while (row >= w.nrow) {
+      row -= w.nrow;
+      ++z;
+    }
+  }
+};
 
 // One kernel per lattice: the code a warp may run holds one velocity set only
 // (instruction-fetch stalls dominated a kernel holding both), and the two
@@ -201,18 +225,13 @@ __global__ void LBM_BATCH_BOUNDS k_batch(BatchInst* inst, const WorkItem* items,
     if (w.kind == KIND_A) {
       for (int node = w.begin + lane; node < w.end; node += 32) wall_node<Q, ST>(p, w.face, node);
     } else {
+      BoxWalk at(w, w.begin + lane);
       if (w.kind == KIND_I) {
-        for (int c = w.begin + lane; c < w.end; c += 32) {
-          int x, y, z;
-          item_cell(w, c, &x, &y, &z);
-          bulk_interior<Q, ST>(p, x, y, z);
-        }
+        for (int c = w.begin + lane; c < w.end; c += 32, at.next(w))
+          bulk_interior<Q, ST>(p, at.x(w), at.y(w), at.z);
       } else {
-        for (int c = w.begin + lane; c < w.end; c += 32) {
-          int x, y, z;
-          item_cell(w, c, &x, &y, &z);
-          bulk_cell<Q, ST, true>(p, x, y, z);
-        }
+        for (int c = w.begin + lane; c < w.end; c += 32, at.next(w))
+          bulk_cell<Q, ST, true>(p, at.x(w), at.y(w), at.z);
       }
     }
     __syncwarp();

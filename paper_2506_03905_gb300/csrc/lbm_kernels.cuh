@@ -86,17 +86,16 @@ __device__ __forceinline__ void interior_finish(const Params& p, const NbOff& o,
   st_rec(vd, o.id, u[0], u[1], u[2], ntn);
 }
 
+// Pull streaming (Eq. 3) of a cell with in-lattice or periodic neighbours:
+// g_i = f*_i(x - c_i) in the raw storage scale.
 template <int Q, int ST>
-__device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int z) {
+__device__ __forceinline__ void pull_interior(const Params& p, const NbOff& o,
+                                              typename Compute<ST>::R (&g)[Q]) {
   using L = Lat<Q>;
   using C = Codec<ST>;
   using R = typename Compute<ST>::R;
   using T = typename C::T;
   const T* LBM_RESTRICT fs = (const T*)p.f_src;
-  const NbOff o = nb_offsets(p, x, y, z);
-  // pull streaming (Eq. 3): source x - c_i; issued first so that the loads are
-  // in flight while the SA stencil is evaluated
-  R g[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
@@ -104,6 +103,15 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
                     (cz > 0 ? o.ozm : (cz < 0 ? o.ozp : 0));
     g[i] = (R)C::ld_raw(fs + (i * o.nc + o.id + off));
   }
+}
+
+template <int Q, int ST>
+__device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int z) {
+  using R = typename Compute<ST>::R;
+  const NbOff o = nb_offsets(p, x, y, z);
+  // the pulled loads are issued first, in flight while the SA stencil is evaluated
+  R g[Q];
+  pull_interior<Q, ST>(p, o, g);
   interior_finish<Q, ST>(p, o, g, x, y);
 }
 
