@@ -386,6 +386,8 @@ def batched_variant(pkg, torch, steps, rank=0, world=1, storage="fp32"):
                                      "instances": len(cases), "cells": total,
                                      "alg_bytes_per_cell": round(alg / total, 1),
                                      "frac_of_hbm": round(alg * steps / bt / 1e9 / peak, 4),
+                                     "mode": "multi-instance launches" if info["mode"] == 1
+                                             else "persistent kernel",
                                      "use_graph": info["use_graph"], "threads": info["threads"],
                                      "tile": info["tile"], "items_per_step": info["items_per_step"],
                                      "status": int(st)}

@@ -310,14 +310,17 @@ lbm_status lbm_moments_noalloc(const void* f, int lattice, int storage, int nx, 
  * Batched sweeps (a mesh-sensitivity sweep of many channel and plate
  * instances; the paper runs its grid and Reynolds-number studies of Sections
  * 4.1.2.4 and 4.1.2.6 as separate runs).  Many independent contexts are
- * advanced together by one persistent, cooperative kernel launch per
- * lbm_batch_step call, replayed from a captured CUDA graph.  Work items, each
- * taken by one warp in a fixed order from a ticket counter, are chunks of 32
- * wall nodes (the wall pre-pass) and ranges of cells of one instance; an item
- * waits only for the items of its own instance it depends on (the previous
- * step, or this step's wall pre-pass for the wall rows), with bounded waits
- * that report LBM_ETIMEOUT.  Each step of an instance computes what lbm_step
- * computes.  Instances keep their own configurations and boundary conditions;
+ * advanced together, in one of two modes.  Mode 0: one persistent, cooperative
+ * kernel launch per lbm_batch_step call, replayed from a captured CUDA graph;
+ * work items, each taken by one warp in a fixed order from a ticket counter,
+ * are chunks of 32 wall nodes (the wall pre-pass) and ranges of cells of one
+ * instance; an item waits only for the items of its own instance it depends
+ * on (the previous step, or this step's wall pre-pass for the wall rows), with
+ * bounded waits that report LBM_ETIMEOUT.  Mode 1: per step, one launch per
+ * kind of item over every instance (wall pre-pass, then wall rows, beside the
+ * face-free cells), one CTA per item, replayed from captured chunks of 32
+ * steps; no device-side waits.  The autotuner picks the faster mode.  Each
+ * step of an instance computes what lbm_step computes.  Instances keep their own configurations and boundary conditions;
  * the contexts must have been created and initialised (lbm_set_fields) first,
  * must share one storage type and one stream, and are read back with
  * lbm_fields / lbm_diagnostics.  The batch does not own the contexts; destroy
@@ -332,14 +335,20 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** out);
    without waiting for the GPU).  The tile size (cells per work item, one warp
    each) and threads per CTA are chosen by the built-in autotuner on the first
    call unless lbm_batch_tune fixed them; the autotuner advances every instance
-   while it times (24 steps).  A bounded wait of an earlier launch that gave up
+   while it times (28 steps).  A bounded wait of an earlier launch that gave up
    is reported here (LBM_ETIMEOUT) once that launch has finished, or by
    lbm_batch_wait; the instances' states are then not valid. */
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
 /* Time the candidate tile sizes (64, 256, 1024 cells per warp item) and block
-   sizes (128, 256 threads) once and keep the fastest; best[0] = threads per
-   CTA, best[1] = cells per tile (best may be NULL).  Synchronises. */
+   sizes (128, 256 threads) of mode 0 and the launches of mode 1 once, keep the
+   fastest configuration of mode 0 and the faster mode (unless
+   lbm_batch_set_mode fixed it); best[0] = threads per CTA, best[1] = cells per
+   tile of mode 0 (best may be NULL).  Advances every instance by 28 steps.
+   Synchronises. */
 lbm_status lbm_batch_tune(lbm_batch* b, int best[2]);
+/* mode 0: the persistent ticketed kernel, 1: per-step multi-instance launches,
+   -1: the autotuner's choice (default).  The paper has no counterpart. */
+lbm_status lbm_batch_set_mode(lbm_batch* b, int mode);
 /* Wait for the batch's launches to finish; LBM_ETIMEOUT if a bounded wait of
    the last launch gave up. */
 lbm_status lbm_batch_wait(lbm_batch* b);
@@ -351,8 +360,9 @@ lbm_status lbm_batch_wait(lbm_batch* b);
 lbm_status lbm_batch_set_wait_limit(lbm_batch* b, long long polls);
 /* out[0] = threads per CTA, out[1] = cells per work item, out[2] = 1 if the
    launches are replayed from a captured graph (0: launched directly because
-   capture was refused), out[3] = work items per step. */
-lbm_status lbm_batch_info(const lbm_batch* b, int out[4]);
+   capture was refused), out[3] = work items per step, out[4] = the mode the
+   steps run in (0 or 1, see lbm_batch_set_mode). */
+lbm_status lbm_batch_info(const lbm_batch* b, int out[5]);
 void lbm_batch_destroy(lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);
 

@@ -27,7 +27,7 @@ __all__ = [
     "lbm_last_error", "lbm_lattice_params", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tune", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_moments_noalloc",
     "lbm_kernel_launches", "lbm_run_to_convergence", "lbm_batch_wait", "lbm_batch_set_wait_limit",
-    "lbm_batch_info", "lbm_steps_done", "lbm_set_wait_limit",
+    "lbm_batch_info", "lbm_steps_done", "lbm_set_wait_limit", "lbm_batch_set_mode",
 ]
 
 LIB_PATH = _build.LIB
@@ -133,6 +133,7 @@ def lib():
         "lbm_batch_wait": (ctypes.c_int, [_P]),
         "lbm_batch_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
         "lbm_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+        "lbm_batch_set_mode": (ctypes.c_int, [_P, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -271,12 +272,20 @@ def lbm_batch_set_wait_limit(b, polls: int):
 
 
 def lbm_batch_info(b):
-    """dict(threads, tile, use_graph, items_per_step) of a batch."""
-    out = (ctypes.c_int * 4)()
+    """dict(threads, tile, use_graph, items_per_step, mode) of a batch."""
+    out = (ctypes.c_int * 5)()
     st = lib().lbm_batch_info(b, out)
     if st != LBM_OK:
         raise LbmError(st, "lbm_batch_info", lbm_batch_last_error(b))
-    return dict(threads=out[0], tile=out[1], use_graph=bool(out[2]), items_per_step=out[3])
+    return dict(threads=out[0], tile=out[1], use_graph=bool(out[2]), items_per_step=out[3],
+                mode=out[4])
+
+
+def lbm_batch_set_mode(b, mode: int):
+    """0: persistent ticketed kernel, 1: per-step multi-instance launches, -1: autotuned."""
+    st = lib().lbm_batch_set_mode(b, int(mode))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_batch_set_mode", lbm_batch_last_error(b))
 
 
 def lbm_steps_done(ctx) -> int:

@@ -29,6 +29,11 @@
 // item of the launch, so a captured launch can be replayed without host
 // updates.  The counters are cleared by a memset captured with the launch.
 //
+// A second mode (lbm_batch_set_mode, or the autotuner's choice) advances the
+// same items by ordinary launches, per step and group one kernel per item
+// kind over every instance (k_multi_a, k_multi_cells), with the wall branch on
+// a second stream; see "Multi-instance launches" below.
+//
 // This translation unit reads, within one launch, data that other warps wrote
 // earlier in the same launch; it defines LBM_COHERENT_LOADS so that those
 // loads are plain global loads, ordered by the fences around the counters.
@@ -258,6 +263,74 @@ template <int Q> BatchKernel batch_kernel_q(int st) {
 }
 BatchKernel batch_kernel(int st, int q) { return q == 19 ? batch_kernel_q<19>(st) : batch_kernel_q<9>(st); }
 
+// ---------------------------------------------------------------------------
+// Multi-instance launches (mode 1).  Per step and lattice group three kernels
+// run over the items of every instance, one CTA per item: the wall pre-pass
+// (A items of kMultiNodes nodes) followed by the wall rows and x-face columns
+// (W and B items) on a second stream, and the face-free cells (I items) on
+// the batch's stream beside them; the branches join before the next step.
+// Kernel boundaries order the steps, so there are no device-side waits, and
+// each kernel has the register budget of its own work.
+// ---------------------------------------------------------------------------
+constexpr int kMultiCells = 256;   // cells per B / I / W item, one per thread
+constexpr int kMultiNodes = 128;   // wall nodes per A item, one per thread
+enum { MK_A = 0, MK_I = 1, MK_BW = 2 };
+
+// The instance's parameters for the item's step, copied to shared memory by the CTA.
+__device__ __forceinline__ const Params& cta_params(Params* sp, const BatchInst& b, int step) {
+  static_assert(sizeof(Params) % sizeof(int) == 0, "Params is copied as ints");
+  const int* s = reinterpret_cast<const int*>(&b.p[(b.cur + step) & 1]);
+  int* d = reinterpret_cast<int*>(sp);
+  for (int k = threadIdx.x; k < (int)(sizeof(Params) / sizeof(int)); k += blockDim.x) d[k] = s[k];
+  __syncthreads();
+  return *sp;
+}
+
+template <int ST, int Q>
+__global__ void __launch_bounds__(kMultiNodes, 8) k_multi_a(const BatchInst* inst, const WorkItem* items,
+                                                            int step) {
+  __shared__ Params sp;
+  const WorkItem w = items[blockIdx.x];
+  const Params& p = cta_params(&sp, inst[w.inst], step);
+  const int node = w.begin + threadIdx.x;
+  if (node < w.end) wall_node<Q, ST>(p, w.face, node);
+}
+
+template <int ST, int Q, bool FACE_FREE>
+__global__ void __launch_bounds__(kMultiCells, 4) k_multi_cells(const BatchInst* inst,
+                                                                const WorkItem* items, int step) {
+  __shared__ Params sp;
+  const WorkItem w = items[blockIdx.x];
+  const Params& p = cta_params(&sp, inst[w.inst], step);
+  const int c = w.begin + threadIdx.x;
+  if (c >= w.end) return;
+  const BoxWalk at(w, c);
+  if (FACE_FREE) bulk_interior<Q, ST>(p, at.x(w), at.y(w), at.z);
+  else bulk_cell<Q, ST, true>(p, at.x(w), at.y(w), at.z);
+}
+
+// Buffer parities of every instance advanced by the steps of a launch sequence.
+__global__ void k_multi_advance(BatchInst* inst, int n, int nsteps) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) inst[k].cur = (inst[k].cur + nsteps) & 1;
+}
+
+using MultiKernel = void (*)(const BatchInst*, const WorkItem*, int);
+template <int Q, int ST> MultiKernel multi_kernel_st(int kind) {
+  return kind == MK_A ? k_multi_a<ST, Q> : (kind == MK_I ? k_multi_cells<ST, Q, true> : k_multi_cells<ST, Q, false>);
+}
+template <int Q> MultiKernel multi_kernel_q(int st, int kind) {
+  switch (st) {
+    case ST_FP32: return multi_kernel_st<Q, ST_FP32>(kind);
+    case ST_FP16: return multi_kernel_st<Q, ST_FP16>(kind);
+    case ST_BF16: return multi_kernel_st<Q, ST_BF16>(kind);
+    default: return multi_kernel_st<Q, ST_FP64>(kind);
+  }
+}
+MultiKernel multi_kernel(int st, int q, int kind) {
+  return q == 19 ? multi_kernel_q<19>(st, kind) : multi_kernel_q<9>(st, kind);
+}
+
 std::string g_batch_err;
 
 }  // namespace
@@ -287,6 +360,17 @@ struct lbm_batch {
   BatchCtl* h_ctl = nullptr;     // pinned copy of the groups' control blocks after each launch
   cudaEvent_t ev_ctl = nullptr;
   bool ctl_pending = false;      // a launch's control copy has not been inspected yet
+  // mode 1 (multi-instance launches): items per group and kind (MK_A, MK_I, MK_BW)
+  int mode = 0;                  // 0: persistent ticketed kernel, 1: multi-instance launches
+  int forced_mode = -1;          // lbm_batch_set_mode; -1: the autotuner's choice
+  WorkItem* d_mitems = nullptr;
+  int moff[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  int mn[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  cudaStream_t side = nullptr;   // wall branch of a multi-instance step
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int prio_hi = 0;
+  cudaGraphExec_t mgexec = nullptr;   // a captured chunk of multi-instance steps
+  int mg_nsteps = -1;
   std::string err;
 };
 
@@ -303,6 +387,10 @@ static void drop_graph(lbm_batch* b) {
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
+  }
+  if (b->mgexec) {
+    cudaGraphExecDestroy(b->mgexec);
+    b->mgexec = nullptr;
   }
 }
 
@@ -322,7 +410,7 @@ static void push_box(std::vector<WorkItem>& items, int inst, int kind, int tile,
 }
 
 static void group_items(const lbm_batch* b, int g, int tile, std::vector<WorkItem>& items,
-                        std::vector<int>& per_a) {
+                        std::vector<int>& per_a, int achunk = 32) {
   std::vector<int> order;
   for (int i = 0; i < (int)b->ctxs.size(); ++i)
     if (b->ctxs[i]->Q == group_q(g)) order.push_back(i);
@@ -331,8 +419,8 @@ static void group_items(const lbm_batch* b, int g, int tile, std::vector<WorkIte
     for (int f = 0; f < 2; ++f) {
       if (!c->base.wall[f]) continue;
       const int nw = c->base.nwall[f];
-      for (int a = 0; a < nw; a += 32) {
-        items.push_back({i, KIND_A, f, a, std::min(nw, a + 32), 0, 0, 0, 0, 0, 0, 0});
+      for (int a = 0; a < nw; a += achunk) {
+        items.push_back({i, KIND_A, f, a, std::min(nw, a + achunk), 0, 0, 0, 0, 0, 0, 0});
         ++per_a[i];
       }
     }
@@ -383,6 +471,113 @@ static lbm_status build_items(lbm_batch* b, int tile) {
   BATCH_TRY(b, cudaStreamSynchronize(b->stream));
   b->tile = tile;
   drop_graph(b);
+  return LBM_OK;
+}
+
+// The items of the multi-instance mode, per group split by kernel: A, I, then
+// B and W (one CTA each).
+static lbm_status build_multi_items(lbm_batch* b) {
+  std::vector<WorkItem> all, items;
+  std::vector<int> per_a(b->ctxs.size(), 0);
+  for (int g = 0; g < 2; ++g) {
+    all.clear();
+    group_items(b, g, kMultiCells, all, per_a, kMultiNodes);
+    for (int kind = 0; kind < 3; ++kind) {
+      b->moff[g][kind] = (int)items.size();
+      for (const WorkItem& w : all) {
+        const int k = w.kind == KIND_A ? MK_A : (w.kind == KIND_I ? MK_I : MK_BW);
+        if (k == kind) items.push_back(w);
+      }
+      b->mn[g][kind] = (int)items.size() - b->moff[g][kind];
+    }
+  }
+  if (b->d_mitems) cudaFree(b->d_mitems);
+  b->d_mitems = nullptr;
+  BATCH_TRY(b, cudaMalloc(&b->d_mitems, std::max<size_t>(1, items.size()) * sizeof(WorkItem)));
+  BATCH_TRY(b, cudaMemcpy(b->d_mitems, items.data(), items.size() * sizeof(WorkItem),
+                          cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+static cudaError_t launch_multi_kernel(lbm_batch* b, int g, int kind, int step, cudaStream_t s, int prio) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(b->mn[g][kind], 1, 1);
+  cfg.blockDim = dim3(kind == MK_A ? kMultiNodes : kMultiCells, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = prio;
+  cfg.attrs = attr;
+  cfg.numAttrs = prio != 0 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, multi_kernel(b->st, group_q(g), kind), (const BatchInst*)b->d_inst,
+                            (const WorkItem*)b->d_mitems + b->moff[g][kind], step);
+}
+
+// Enqueue nsteps multi-instance steps on s: per step the wall branch (A, then
+// B / W items) on the side stream at the highest priority beside the I items,
+// joined before the next step; then the parities advance.
+static lbm_status launch_multi(lbm_batch* b, int nsteps, cudaStream_t s) {
+  for (int step = 0; step < nsteps; ++step) {
+    BATCH_TRY(b, cudaEventRecord(b->ev_fork, s));
+    BATCH_TRY(b, cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+    for (int g = 0; g < 2; ++g)
+      if (b->mn[g][MK_A] > 0) BATCH_TRY(b, launch_multi_kernel(b, g, MK_A, step, b->side, b->prio_hi));
+    for (int g = 0; g < 2; ++g)
+      if (b->mn[g][MK_BW] > 0) BATCH_TRY(b, launch_multi_kernel(b, g, MK_BW, step, b->side, b->prio_hi));
+    for (int g = 0; g < 2; ++g)
+      if (b->mn[g][MK_I] > 0) BATCH_TRY(b, launch_multi_kernel(b, g, MK_I, step, s, 0));
+    BATCH_TRY(b, cudaEventRecord(b->ev_join, b->side));
+    BATCH_TRY(b, cudaStreamWaitEvent(s, b->ev_join, 0));
+  }
+  const int n = (int)b->ctxs.size();
+  k_multi_advance<<<(n + 255) / 256, 256, 0, s>>>(b->d_inst, n, nsteps);
+  BATCH_TRY(b, cudaGetLastError());
+  return LBM_OK;
+}
+
+static void advance_host_parity(lbm_batch* b, int nsteps);
+
+// Multi-instance steps from captured chunks of up to kMultiChunk steps (the
+// remainder launched directly).
+constexpr int kMultiChunk = 32;
+static lbm_status step_multi(lbm_batch* b, int nsteps) {
+  const int chunk = std::min(nsteps, kMultiChunk);
+  int left = nsteps;
+  if (b->use_graph && left >= chunk) {
+    if (!b->mgexec || b->mg_nsteps != chunk) {
+      if (b->mgexec) cudaGraphExecDestroy(b->mgexec);
+      b->mgexec = nullptr;
+      cudaStream_t cap;
+      BATCH_TRY(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      lbm_status s = LBM_OK;
+      if (e == cudaSuccess) {
+        s = launch_multi(b, chunk, cap);
+        e = cudaStreamEndCapture(cap, &g);
+        if (s == LBM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->mgexec, g, 0);
+      }
+      if (g) cudaGraphDestroy(g);
+      cudaStreamDestroy(cap);
+      if (e != cudaSuccess || s != LBM_OK || !b->mgexec) {
+        // capture refused: launch directly from now on
+        cudaGetLastError();
+        if (b->mgexec) cudaGraphExecDestroy(b->mgexec);
+        b->mgexec = nullptr;
+        b->mg_nsteps = -1;
+        b->use_graph = false;
+      } else {
+        b->mg_nsteps = chunk;
+      }
+    }
+    if (b->mgexec)
+      for (; left >= chunk; left -= chunk) BATCH_TRY(b, cudaGraphLaunch(b->mgexec, b->stream));
+  }
+  if (left > 0) {
+    lbm_status s = launch_multi(b, left, b->stream);
+    if (s != LBM_OK) return s;
+  }
+  advance_host_parity(b, nsteps);
   return LBM_OK;
 }
 
@@ -544,10 +739,18 @@ extern "C" lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** 
     b->h_inst[i].cur = c->cur;
   }
   b->ctl_bytes = 2 * sizeof(BatchCtl) + 2 * (size_t)n * sizeof(unsigned);
+  {
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) hi = 0;
+    b->prio_hi = hi;
+  }
   if (cudaMalloc(&b->d_inst, n * sizeof(BatchInst)) != cudaSuccess ||
       cudaMalloc(&b->d_ctl, b->ctl_bytes) != cudaSuccess ||
       cudaMallocHost(&b->h_ctl, 2 * sizeof(BatchCtl)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_ctl, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->ev_ctl, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, b->prio_hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     g_batch_err = "lbm_batch_create: device allocation failed";
     lbm_batch_destroy(b);
     return LBM_ENOMEM;
@@ -565,6 +768,7 @@ extern "C" lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** 
   }
   lbm_status st = set_threads(b, 256);
   if (st == LBM_OK) st = build_items(b, 256);
+  if (st == LBM_OK) st = build_multi_items(b);
   if (st != LBM_OK) {
     g_batch_err = b->err;
     lbm_batch_destroy(b);
@@ -614,9 +818,29 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int best[2]) {
     }
     if (s != LBM_OK && s != LBM_EUNSUPPORTED) break;
   }
+  if (s != LBM_OK && s != LBM_EUNSUPPORTED) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
+  }
+  // the multi-instance launches, timed the same way (uncaptured)
+  float multi_ms = 1e30f;
+  s = launch_multi(b, 1, b->stream);
+  if (s == LBM_OK) {
+    advance_host_parity(b, 1);
+    BATCH_TRY(b, cudaEventRecord(e0, b->stream));
+    s = launch_multi(b, trial, b->stream);
+  }
+  if (s == LBM_OK) {
+    advance_host_parity(b, trial);
+    BATCH_TRY(b, cudaEventRecord(e1, b->stream));
+    BATCH_TRY(b, cudaEventSynchronize(e1));
+    BATCH_TRY(b, cudaEventElapsedTime(&multi_ms, e0, e1));
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (s != LBM_OK && s != LBM_EUNSUPPORTED) return s;
+  if (s != LBM_OK) return s;
+  b->mode = b->forced_mode >= 0 ? b->forced_mode : (multi_ms < best_ms ? 1 : 0);
   s = set_threads(b, bt);
   if (s == LBM_OK) s = build_items(b, btile);
   if (s != LBM_OK) return s;
@@ -640,6 +864,7 @@ extern "C" lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
     s = lbm_batch_tune(b, nullptr);
     if (s != LBM_OK) return s;
   }
+  if (b->mode == 1) return step_multi(b, nsteps);
   if (!b->use_graph) return launch_tracked(b, nsteps);
   // one persistent launch per call, replayed from a graph while nsteps repeats
   if (!b->gexec || b->g_nsteps != nsteps) {
@@ -684,12 +909,24 @@ extern "C" lbm_status lbm_batch_set_wait_limit(lbm_batch* b, long long polls) {
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_batch_info(const lbm_batch* b, int out[4]) {
+extern "C" lbm_status lbm_batch_info(const lbm_batch* b, int out[5]) {
   if (!b || !out) return LBM_EINVAL;
-  out[0] = b->threads;
-  out[1] = b->tile;
+  const bool multi = b->mode == 1;
+  out[0] = multi ? kMultiCells : b->threads;
+  out[1] = multi ? kMultiCells : b->tile;
   out[2] = b->use_graph ? 1 : 0;
-  out[3] = b->nitems[0] + b->nitems[1];
+  out[3] = multi ? b->mn[0][0] + b->mn[0][1] + b->mn[0][2] + b->mn[1][0] + b->mn[1][1] + b->mn[1][2]
+                 : b->nitems[0] + b->nitems[1];
+  out[4] = b->mode;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_set_mode(lbm_batch* b, int mode) {
+  if (!b || mode < -1 || mode > 1) return LBM_EINVAL;
+  lbm_status s = poll_ctl(b, true);
+  if (s != LBM_OK) return s;
+  b->forced_mode = mode;
+  if (mode >= 0) b->mode = mode;
   return LBM_OK;
 }
 
@@ -702,6 +939,13 @@ extern "C" void lbm_batch_destroy(lbm_batch* b) {
   if (b->d_items) cudaFree(b->d_items);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
   if (b->ev_ctl) cudaEventDestroy(b->ev_ctl);
+  if (b->d_mitems) cudaFree(b->d_mitems);
+  if (b->side) {
+    cudaStreamSynchronize(b->side);
+    cudaStreamDestroy(b->side);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   delete b;
 }
 

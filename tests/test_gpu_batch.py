@@ -1,8 +1,9 @@
-"""Batched sweeps: one persistent cooperative launch advancing many instances.
+"""Batched sweeps: many instances advanced together, by one persistent
+cooperative launch (mode 0) or by per-step multi-instance launches (mode 1).
 
-The batch must give what each instance gives when stepped alone (same
-arithmetic; compiled in a different kernel, so agreement is to rounding), and
-the instances must still match the FP64 oracle.
+In either mode the batch must give what each instance gives when stepped alone
+(same arithmetic; compiled in different kernels, so agreement is to rounding),
+and the instances must still match the FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -44,10 +45,12 @@ def solvers(cases):
 FIELDS = ["u", "nu_t", "u_tau_ymin"]
 
 
-TUNE_STEPS = 6 * 4    # lbm_batch_tune: 2 block sizes x 3 tiles, each 1 warm-up + 3 timed steps
+# lbm_batch_tune: mode 0's 2 block sizes x 3 tiles and mode 1, each 1 warm-up + 3 timed steps
+TUNE_STEPS = 7 * 4
 
 
-def test_batch_matches_single_instances_and_oracle():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_matches_single_instances_and_oracle(mode):
     import paper_2506_03905_gb300 as pkg
     cases = mixed_cases()
     nsteps = 40
@@ -59,8 +62,11 @@ def test_batch_matches_single_instances_and_oracle():
         s.close()
     batch_s = solvers(cases)
     b = pkg.lbm_batch_create([s.ctx for s in batch_s])
+    pkg.lbm_batch_set_mode(b, mode)
     threads, tile = pkg.lbm_batch_tune(b)          # tuning advances every instance
     assert threads in (128, 256) and tile in (64, 256, 1024)   # cells per warp item
+    assert batch_s[0].steps_done() == TUNE_STEPS
+    assert pkg.lbm_batch_info(b)["mode"] == mode
     pkg.lbm_batch_step(b, nsteps - TUNE_STEPS - 5)
     pkg.lbm_batch_step(b, 5)
     got = [s.fields(FIELDS) for s in batch_s]
@@ -77,12 +83,13 @@ def test_batch_matches_single_instances_and_oracle():
             assert rel(g[k], o[k]) < 1e-5, (c.name, k, rel(g[k], o[k]))
 
 
-def test_batch_interleaved_with_single_steps():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_interleaved_with_single_steps(mode):
     """Stepping the members on their own between batch launches keeps every
     instance's buffer parity right."""
     import paper_2506_03905_gb300 as pkg
     cases = mixed_cases()[:3]
-    nsteps = TUNE_STEPS + 1 + 5
+    nsteps = TUNE_STEPS + 1 + 5 + 33     # 33: a captured chunk of 32 steps plus one direct step
     a = solvers(cases)
     for s in a:
         s.step(nsteps)
@@ -91,10 +98,12 @@ def test_batch_interleaved_with_single_steps():
         s.close()
     bs = solvers(cases)
     b = pkg.lbm_batch_create([s.ctx for s in bs])
+    pkg.lbm_batch_set_mode(b, mode)
     pkg.lbm_batch_tune(b)
     for s in bs:
         s.step(1)                  # odd number of single steps: parity flips
     pkg.lbm_batch_step(b, 5)
+    pkg.lbm_batch_step(b, 33)
     got = [s.fields(["u"])["u"] for s in bs]
     pkg.lbm_batch_destroy(b)
     for s in bs:

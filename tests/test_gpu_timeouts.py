@@ -34,7 +34,9 @@ def test_batch_wait_runs_out_and_the_batch_recovers():
     cases = mixed_cases()
     ss = solvers(cases)
     b = pkg.lbm_batch_create([s.ctx for s in ss])
+    pkg.lbm_batch_set_mode(b, 0)      # the persistent kernel: the mode with device-side waits
     pkg.lbm_batch_tune(b)
+    assert pkg.lbm_batch_info(b)["mode"] == 0
     assert pkg.lbm_batch_wait(b) == pkg.LBM_OK
     pkg.lbm_batch_set_wait_limit(b, 0)
     pkg.lbm_batch_step(b, 3)          # enqueued; the failure is reported by the wait
