@@ -272,7 +272,11 @@ BatchKernel batch_kernel(int st, int q) { return q == 19 ? batch_kernel_q<19>(st
 // Kernel boundaries order the steps, so there are no device-side waits, and
 // each kernel has the register budget of its own work.
 // ---------------------------------------------------------------------------
-constexpr int kMultiCells = 256;   // cells per B / I / W item, one per thread
+#ifndef LBM_MULTI_CELLS
+#define LBM_MULTI_CELLS 128
+#endif
+constexpr int kMultiCells = LBM_MULTI_CELLS;   // cells per B / I / W item, one per thread
+constexpr int kMultiCellsMinB = 16384 / LBM_MULTI_CELLS;   // 64 registers
 constexpr int kMultiNodes = 128;   // wall nodes per A item, one per thread
 enum { MK_A = 0, MK_I = 1, MK_BW = 2 };
 
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kMultiNodes, 8) k_multi_a(const BatchInst* ins
 }
 
 template <int ST, int Q, bool FACE_FREE>
-__global__ void __launch_bounds__(kMultiCells, 4) k_multi_cells(const BatchInst* inst,
+__global__ void __launch_bounds__(kMultiCells, kMultiCellsMinB) k_multi_cells(const BatchInst* inst,
                                                                 const WorkItem* items, int step) {
   __shared__ Params sp;
   const WorkItem w = items[blockIdx.x];
@@ -540,10 +544,13 @@ static void advance_host_parity(lbm_batch* b, int nsteps);
 // Multi-instance steps from captured chunks of up to kMultiChunk steps (the
 // remainder launched directly).
 constexpr int kMultiChunk = 32;
+#ifndef LBM_MULTI_GRAPH
+#define LBM_MULTI_GRAPH 1
+#endif
 static lbm_status step_multi(lbm_batch* b, int nsteps) {
   const int chunk = std::min(nsteps, kMultiChunk);
   int left = nsteps;
-  if (b->use_graph && left >= chunk) {
+  if (LBM_MULTI_GRAPH && b->use_graph && left >= chunk) {
     if (!b->mgexec || b->mg_nsteps != chunk) {
       if (b->mgexec) cudaGraphExecDestroy(b->mgexec);
       b->mgexec = nullptr;
