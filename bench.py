@@ -297,9 +297,10 @@ def run_ours(args):
                 "alg_bytes_per_cell": ALG_BYTES[(pc.lattice, pc.storage)],
                 "bulk_frac_of_hbm": round(pb / (pbulk * 1e-3) / 1e9 / peak, 4),
                 "nonfinite": int(pd.nonfinite)}
+        bsteps = max(10, min(args.steps, 300))   # the sweep's steps are short: 300 for a stable figure
         for storage in ("fp32", "fp16"):
             try:
-                variants.update(batched_variant(pkg, torch, vsteps, storage=storage))
+                variants.update(batched_variant(pkg, torch, bsteps, storage=storage))
             except Exception as exc:  # the batched path reports its own status
                 variants[f"batched_{storage}"] = {"unavailable": str(exc)[:200]}
 

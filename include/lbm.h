@@ -318,8 +318,8 @@ lbm_status lbm_moments_noalloc(const void* f, int lattice, int storage, int nx, 
  * on (the previous step, or this step's wall pre-pass for the wall rows), with
  * bounded waits that report LBM_ETIMEOUT.  Mode 1: per step, one launch per
  * kind of item over every instance (wall pre-pass, then wall rows, beside the
- * face-free cells), one CTA per item, replayed from captured chunks of 32
- * steps; no device-side waits.  The autotuner picks the faster mode.  Each
+ * face-free cells), one CTA per item, launched directly (the wall branch's
+ * stream priority holds only for direct launches); no device-side waits.  The autotuner picks the faster mode.  Each
  * step of an instance computes what lbm_step computes.  Instances keep their own configurations and boundary conditions;
  * the contexts must have been created and initialised (lbm_set_fields) first,
  * must share one storage type and one stream, and are read back with
@@ -359,9 +359,9 @@ lbm_status lbm_batch_wait(lbm_batch* b);
    counterpart. */
 lbm_status lbm_batch_set_wait_limit(lbm_batch* b, long long polls);
 /* out[0] = threads per CTA, out[1] = cells per work item, out[2] = 1 if the
-   launches are replayed from a captured graph (0: launched directly because
-   capture was refused), out[3] = work items per step, out[4] = the mode the
-   steps run in (0 or 1, see lbm_batch_set_mode). */
+   launches are replayed from a captured graph (mode 0; 0 in mode 1, whose
+   launches are direct, or if capture was refused), out[3] = work items per
+   step, out[4] = the mode the steps run in (0 or 1, see lbm_batch_set_mode). */
 lbm_status lbm_batch_info(const lbm_batch* b, int out[5]);
 void lbm_batch_destroy(lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);

@@ -269,6 +269,7 @@ BatchKernel batch_kernel(int st, int q) { return q == 19 ? batch_kernel_q<19>(st
 // (A items of kMultiNodes nodes) followed by the wall rows and x-face columns
 // (W and B items) on a second stream, and the face-free cells (I items) on
 // the batch's stream beside them; the branches join before the next step.
+// The launches are direct (not captured: see step_multi).
 // Kernel boundaries order the steps, so there are no device-side waits, and
 // each kernel has the register budget of its own work.
 // ---------------------------------------------------------------------------
@@ -373,8 +374,6 @@ struct lbm_batch {
   cudaStream_t side = nullptr;   // wall branch of a multi-instance step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int prio_hi = 0;
-  cudaGraphExec_t mgexec = nullptr;   // a captured chunk of multi-instance steps
-  int mg_nsteps = -1;
   std::string err;
 };
 
@@ -391,10 +390,6 @@ static void drop_graph(lbm_batch* b) {
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
-  }
-  if (b->mgexec) {
-    cudaGraphExecDestroy(b->mgexec);
-    b->mgexec = nullptr;
   }
 }
 
@@ -528,7 +523,7 @@ static lbm_status launch_multi(lbm_batch* b, int nsteps, cudaStream_t s) {
       if (b->mn[g][MK_A] > 0) BATCH_TRY(b, launch_multi_kernel(b, g, MK_A, step, b->side, b->prio_hi));
     for (int g = 0; g < 2; ++g)
       if (b->mn[g][MK_BW] > 0) BATCH_TRY(b, launch_multi_kernel(b, g, MK_BW, step, b->side, b->prio_hi));
-    for (int g = 0; g < 2; ++g)
+    for (int g = 0; g < 2; ++g)   // launched after the wall branch: measured faster than before it
       if (b->mn[g][MK_I] > 0) BATCH_TRY(b, launch_multi_kernel(b, g, MK_I, step, s, 0));
     BATCH_TRY(b, cudaEventRecord(b->ev_join, b->side));
     BATCH_TRY(b, cudaStreamWaitEvent(s, b->ev_join, 0));
@@ -541,49 +536,12 @@ static lbm_status launch_multi(lbm_batch* b, int nsteps, cudaStream_t s) {
 
 static void advance_host_parity(lbm_batch* b, int nsteps);
 
-// Multi-instance steps from captured chunks of up to kMultiChunk steps (the
-// remainder launched directly).
-constexpr int kMultiChunk = 32;
-#ifndef LBM_MULTI_GRAPH
-#define LBM_MULTI_GRAPH 1
-#endif
+// Multi-instance steps, launched directly: the wall branch's stream priority
+// is honoured only by direct launches (captured 32-step chunks replayed from a
+// graph: 26.1k against 27.1k MLUPS on the 96-instance FP32 sweep).
 static lbm_status step_multi(lbm_batch* b, int nsteps) {
-  const int chunk = std::min(nsteps, kMultiChunk);
-  int left = nsteps;
-  if (LBM_MULTI_GRAPH && b->use_graph && left >= chunk) {
-    if (!b->mgexec || b->mg_nsteps != chunk) {
-      if (b->mgexec) cudaGraphExecDestroy(b->mgexec);
-      b->mgexec = nullptr;
-      cudaStream_t cap;
-      BATCH_TRY(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-      cudaGraph_t g = nullptr;
-      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-      lbm_status s = LBM_OK;
-      if (e == cudaSuccess) {
-        s = launch_multi(b, chunk, cap);
-        e = cudaStreamEndCapture(cap, &g);
-        if (s == LBM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->mgexec, g, 0);
-      }
-      if (g) cudaGraphDestroy(g);
-      cudaStreamDestroy(cap);
-      if (e != cudaSuccess || s != LBM_OK || !b->mgexec) {
-        // capture refused: launch directly from now on
-        cudaGetLastError();
-        if (b->mgexec) cudaGraphExecDestroy(b->mgexec);
-        b->mgexec = nullptr;
-        b->mg_nsteps = -1;
-        b->use_graph = false;
-      } else {
-        b->mg_nsteps = chunk;
-      }
-    }
-    if (b->mgexec)
-      for (; left >= chunk; left -= chunk) BATCH_TRY(b, cudaGraphLaunch(b->mgexec, b->stream));
-  }
-  if (left > 0) {
-    lbm_status s = launch_multi(b, left, b->stream);
-    if (s != LBM_OK) return s;
-  }
+  lbm_status s = launch_multi(b, nsteps, b->stream);
+  if (s != LBM_OK) return s;
   advance_host_parity(b, nsteps);
   return LBM_OK;
 }
@@ -921,7 +879,7 @@ extern "C" lbm_status lbm_batch_info(const lbm_batch* b, int out[5]) {
   const bool multi = b->mode == 1;
   out[0] = multi ? kMultiCells : b->threads;
   out[1] = multi ? kMultiCells : b->tile;
-  out[2] = b->use_graph ? 1 : 0;
+  out[2] = !multi && b->use_graph ? 1 : 0;
   out[3] = multi ? b->mn[0][0] + b->mn[0][1] + b->mn[0][2] + b->mn[1][0] + b->mn[1][1] + b->mn[1][2]
                  : b->nitems[0] + b->nitems[1];
   out[4] = b->mode;
