@@ -525,8 +525,11 @@ def run_profile_case(args):
     --steps steps, each launched individually (no graph)."""
     import torch
     import paper_2506_03905_gb300 as pkg
-    case = C.channel_3d(re_tau=5200.0, scheme=args.scheme, nx=args.nx, ny=args.ny, nz=args.nz,
-                        storage=args.storage)
+    if args.plate:
+        case = C.flat_plate_3d(scheme=args.scheme, storage=args.storage)
+    else:
+        case = C.channel_3d(re_tau=5200.0, scheme=args.scheme, nx=args.nx, ny=args.ny, nz=args.nz,
+                            storage=args.storage)
     s = pkg.Solver(case)
     s.set_fields(*C.initial_fields(case))
     s.step_timed(args.warmup)
@@ -581,6 +584,8 @@ def main():
     ap.add_argument("--ny", type=int, default=128)
     ap.add_argument("--nz", type=int, default=64)
     ap.add_argument("--scheme", default="wall_bb")
+    ap.add_argument("--plate", action="store_true",
+                    help="--profile-case on the 2048x512x8 flat plate instead of the channel")
     ap.add_argument("--storage", default="fp32")
     args = ap.parse_args()
     if args.profile_case:

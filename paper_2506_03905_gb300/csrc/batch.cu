@@ -79,7 +79,7 @@ struct WorkItem {
   int face;      // KIND_A: 0 = ymin, 1 = ymax
   int begin, end;   // wall nodes (A) or entries of the box (B, I, W)
   int xa, xs, ncol, ya, ys, nrow;
-  int pad;
+  int nz;        // planes of the box (entries: columns fastest, then planes, then rows)
 };
 
 // Control block of one launch of a lattice group, cleared before it: the ticket
@@ -167,19 +167,22 @@ __device__ __forceinline__ void warp_load_params(Params* dst, const Params* src,
 #endif
 
 // The entries c0, c0 + 32, c0 + 64, ... of a cell item's box (ncol columns of
-// stride xs from xa, nrow rows of stride ys from ya, then planes) as cell
-// coordinates: one division set for the first entry, then carries.
+// stride xs from xa, then the nz planes, then nrow rows of stride ys from ya)
+// as cell coordinates: one division set for the first entry, then carries.
+// Planes before rows: a cell's z neighbours are a row's length away in the
+// entry order and its y neighbours ncol * nz entries away, instead of a whole
+// plane (the re-reads then stay in L2 on large plates).
 struct BoxWalk {
   int col, row, z;
-  int dcol, drow;   // 32 entries = drow rows and dcol columns
+  int dcol, dz;   // 32 entries = dz planes and dcol columns
   __device__ __forceinline__ BoxWalk(const WorkItem& w, int c0) {
-    const int per_z = w.ncol * w.nrow;
-    z = c0 / per_z;
-    const int r = c0 - z * per_z;
-    row = r / w.ncol;
-    col = r - row * w.ncol;
-    drow = 32 / w.ncol;
-    dcol = 32 - drow * w.ncol;
+    const int per_row = w.ncol * w.nz;
+    row = c0 / per_row;
+    const int r = c0 - row * per_row;
+    z = r / w.ncol;
+    col = r - z * w.ncol;
+    dz = 32 / w.ncol;
+    dcol = 32 - dz * w.ncol;
   }
   __device__ __forceinline__ int x(const WorkItem& w) const { return w.xa + col * w.xs; }
   __device__ __forceinline__ int y(const WorkItem& w) const { return w.ya + row * w.ys; }
@@ -187,12 +190,12 @@ struct BoxWalk {
     col += dcol;
     if (col >= w.ncol) {
       col -= w.ncol;
-      ++row;
-    }
-    row += drow;
-    while (row >= w.nrow) {
-      row -= w.nrow;
       ++z;
+    }
+    z += dz;
+    while (z >= w.nz) {
+      z -= w.nz;
+      ++row;
     }
   }
 };
@@ -405,7 +408,7 @@ static void push_box(std::vector<WorkItem>& items, int inst, int kind, int tile,
                      int xs, int ncol, int ya, int ys, int nrow) {
   const int n = ncol * nrow * nz;
   for (int a = 0; a < n; a += tile)
-    items.push_back({inst, kind, 0, a, std::min(n, a + tile), xa, xs, ncol, ya, ys, nrow, 0});
+    items.push_back({inst, kind, 0, a, std::min(n, a + tile), xa, xs, ncol, ya, ys, nrow, nz});
 }
 
 static void group_items(const lbm_batch* b, int g, int tile, std::vector<WorkItem>& items,

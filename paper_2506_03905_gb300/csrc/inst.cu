@@ -63,7 +63,8 @@ static void bulk_st(const Params& p, int rows, bool pairs, dim3 g, dim3 b, cudaS
   // a lattice periodic in x and y
   // (pairs: two cells per thread, and the launch shape of lbm_ctx_bulk_launch_dims
   // covers pairs of cells along x)
-  const bool fast = rows == ROWS_INNER || (rows == ROWS_ALL && p.px && p.py);
+  const int rs = rows & ROWS_MASK;
+  const bool fast = rs == ROWS_INNER || (rs == ROWS_ALL && p.px && p.py);
   if (fast && pairs) launch_prio(k_bulk2<LBM_Q, ST>, g, b, s, prio, p, rows);
   else if (fast) launch_prio(k_bulk<LBM_Q, ST, false>, g, b, s, prio, p, rows);
   else launch_prio(k_bulk<LBM_Q, ST, true>, g, b, s, prio, p, rows);

@@ -64,5 +64,6 @@ struct lbm_ctx {
 void lbm_ctx_set_error(lbm_ctx* c, const char* fmt, ...);
 lbm_status lbm_ctx_finalize(lbm_ctx* c);
 lbm::Params lbm_ctx_params(const lbm_ctx* c, int src);
-void lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b);
+// returns the row-set argument of the launch (rows, with ROWS_ZY for the swapped block order)
+int lbm_ctx_bulk_launch_dims(const lbm_ctx* c, int rows, dim3* g, dim3* b);
 bool lbm_ctx_bulk_pairs(const lbm_ctx* c, int rows);

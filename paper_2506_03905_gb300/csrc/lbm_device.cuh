@@ -52,6 +52,11 @@ enum { FLAG_NONFINITE = 1u, FLAG_NEWTON = 2u, FLAG_TMA_TIMEOUT = 4u };
 // columns 0 and nx-1 of rows 1..ny-2 (the x-face cells of a non-periodic x
 // axis, which both inner-row kernels leave out).
 enum { ROWS_ALL = 0, ROWS_INNER = 1, ROWS_WALL = 2, ROWS_XEDGE = 3 };
+// Flag on a row set: the launch grid holds the z planes in y and the row tiles
+// in z, so that consecutive blocks step through z before y (the blocks that
+// re-read a plane's neighbours then run close together; see
+// lbm_ctx_bulk_launch_dims).
+enum { ROWS_ZY = 16, ROWS_MASK = 15 };
 // threads per k_bulk block (x fastest: 32 x 2 cells for nx >= 32)
 #ifndef LBM_BULK_THREADS
 #define LBM_BULK_THREADS 64

@@ -407,10 +407,12 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
 #define LBM_BULK2_MINB 10
 #endif
 template <int Q, int ST>
-__global__ void __launch_bounds__(LBM_BULK_THREADS, LBM_BULK2_MINB) k_bulk2(const Params p, int rows) {
+__global__ void __launch_bounds__(LBM_BULK_THREADS, LBM_BULK2_MINB) k_bulk2(const Params p, int rows_arg) {
+  const bool zy = rows_arg & ROWS_ZY;
+  const int rows = rows_arg & ROWS_MASK;
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int r = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int r = (zy ? blockIdx.z : blockIdx.y) * blockDim.y + threadIdx.y;
+  const int z = zy ? blockIdx.y : blockIdx.z;
   const int y = rows == ROWS_INNER ? r + 1 : r;
   if (x0 >= p.nx || y >= (rows == ROWS_INNER ? p.ny - 1 : p.ny)) return;
   // x-face columns of a non-periodic x axis belong to the ROWS_XEDGE launch
@@ -422,10 +424,12 @@ __global__ void __launch_bounds__(LBM_BULK_THREADS, LBM_BULK2_MINB) k_bulk2(cons
 }
 
 template <int Q, int ST, bool GENERAL>
-__global__ void LBM_BULK_BOUNDS k_bulk(const Params p, int rows) {
+__global__ void LBM_BULK_BOUNDS k_bulk(const Params p, int rows_arg) {
+  const bool zy = rows_arg & ROWS_ZY;
+  const int rows = rows_arg & ROWS_MASK;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int r = (zy ? blockIdx.z : blockIdx.y) * blockDim.y + threadIdx.y;
+  const int z = zy ? blockIdx.y : blockIdx.z;
   int y = r;
   int xx = x;
   if (rows == ROWS_INNER) y = r + 1;
