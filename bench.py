@@ -327,7 +327,9 @@ def run_ours(args):
                      "kernel_ms": round(inner_avg, 4), "bulk_rows_ms": round(bulk_avg, 4),
                      "wall_pass_ms": round(wall_ms / args.steps, 4)},
         "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "status": int(st)},
+                "d2h_bytes_per_step": int(d2h), "status": int(st),
+                # one FP64 field upload and one read-back per run of this many steps
+                "steps_per_transfer": args.steps},
         "gpu_launches": int(n_launches),
         **({"error": "non-finite state after the timed steps"} if diag.nonfinite else {}),
         "clocks": clk,
