@@ -680,7 +680,8 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
                             p.utau[fi][node], &ut);
     const R utr = (R)ut, inu = psel<R>(p.inv_nu, p.inv_nu_f);
     const R ypB = utr * (R)dw * inu;
-    const R upB = p.turbulent ? utr * wf_uplus_r<R>(p, ypB) : (R)0;   // u_B = u_tau u+(y_B+)
+    const R uplB = p.turbulent ? wf_uplus_r<R>(p, ypB) : (R)0;         // u+(y_B+)
+    const R upB = utr * uplB;                                          // u_B = u_tau u+(y_B+)
     const R uB[3] = {upB * tx, (R)0, upB * tz};
     // Eq. 23 with u_B . n = 0: rho_B = f_par + 2 f_perp (deviations: weights sum to 1)
     R gpar = 0, gperp = 0;
@@ -722,7 +723,7 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
       // Eq. 29: (u_tau / Delta)(-11/6 u+(y_B+) + 3 u+(y_B+ + D+) - 3/2 u+(y_B+ + 2D+)
       //          + 1/3 u+(y_B+ + 3D+)), Delta = 1, D+ = u_tau / nu
       const R dp = utr * inu;
-      ana = ut > 0.0 ? utr * ((R)(-11.0 / 6.0) * wf_uplus_r<R>(p, ypB) +
+      ana = ut > 0.0 ? utr * ((R)(-11.0 / 6.0) * uplB +
                               (R)3 * wf_uplus_r<R>(p, ypB + dp) -
                               (R)1.5 * wf_uplus_r<R>(p, ypB + (R)2 * dp) +
                               wf_uplus_r<R>(p, ypB + (R)3 * dp) * (R)(1.0 / 3.0))
