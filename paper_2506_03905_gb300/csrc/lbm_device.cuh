@@ -592,13 +592,18 @@ __host__ __device__ inline double wf_dudy(int law, double kap, double yp) {
 // Newton inversion (u_B of Section 3.1, the slope of Eq. 15 in Eq. 27, the four
 // values of Eq. 29): a few ulp of FP32 (~1e-7 relative), where the FP64 forms
 // would run on GB300's FP64 pipe at 1/64 of the FP32 rate.
+// atan2(b, s) for b > 0 is pi/2 - atan(s / b) on the whole continuous branch
+// (an absolute error of a few 1e-7 against terms of u+ ~ 10, where the
+// two-argument form's quadrant logic costs more instructions).
 __device__ __forceinline__ float wf_uplus_f(int law, float kap, float B, float yp) {
   if (law == 1) return logf(yp) / kap + B;
   const float s1 = yp + (float)WF::a1, s2 = yp + (float)WF::a2;
   const float b1 = (float)WF::b1, b2 = (float)WF::b2;
+  const float hpi = 1.57079632679489662f;
+  const float t1 = hpi - atanf(s1 * (float)(1.0 / WF::b1));
+  const float t2 = hpi - atanf(s2 * (float)(1.0 / WF::b2));
   return (float)WF::Bb + (float)WF::c1 * logf(s1 * s1 + b1 * b1) -
-         (float)WF::c2 * logf(s2 * s2 + b2 * b2) - (float)WF::c3 * atan2f(b1, s1) -
-         (float)WF::c4 * atan2f(b2, s2);
+         (float)WF::c2 * logf(s2 * s2 + b2 * b2) - (float)WF::c3 * t1 - (float)WF::c4 * t2;
 }
 
 __device__ __forceinline__ float wf_dudy_f(int law, float kap, float yp) {
