@@ -113,10 +113,26 @@ class ClockSampler:
                  "-lms", "20"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        self._wait_lines(1, 5.0)     # nvidia-smi needs a moment before its first sample
+
+    def _lines(self) -> int:
+        try:
+            with open(self.path) as fh:
+                return sum(1 for _ in fh)
+        except OSError:
+            return 0
+
+    def _wait_lines(self, n: int, limit_s: float):
+        t0 = time.perf_counter()
+        while self.proc is not None and self._lines() < n and time.perf_counter() - t0 < limit_s:
+            time.sleep(0.005)
 
     def stop(self):
         if self.proc is None:
             return None
+        # a timed region shorter than the 20 ms sampling period may fall between two
+        # samples: keep the sampler for one more, the one closest after the region
+        self._wait_lines(self._lines() + 1, 1.0)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
