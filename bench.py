@@ -413,6 +413,25 @@ def batched_variant(pkg, torch, steps, rank=0, world=1, storage="fp32"):
                                      "use_graph": info["use_graph"], "threads": info["threads"],
                                      "tile": info["tile"], "items_per_step": info["items_per_step"],
                                      "status": int(st)}
+        # the other mode on the same instances, for comparison: the persistent
+        # ticketed kernel replayed from its captured graph, or the per-step launches
+        other = 0 if info["mode"] == 1 else 1
+        pkg.lbm_batch_set_mode(b, other)
+        pkg.lbm_batch_step(b, steps)          # captures the graph of the new mode
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pkg.lbm_batch_step(b, steps)
+        torch.cuda.synchronize()
+        ot = time.perf_counter() - t0
+        oinfo = pkg.lbm_batch_info(b)
+        ost = pkg.lbm_batch_wait(b)
+        key = "persistent" if other == 0 else "multi_launch"
+        out[f"batched_{storage}_{key}"] = {
+            "mlups": round(total * steps / ot / 1e6, 1),
+            "frac_of_hbm": round(alg * steps / ot / 1e9 / peak, 4),
+            "mode": "persistent kernel" if other == 0 else "multi-instance launches",
+            "use_graph": oinfo["use_graph"], "threads": oinfo["threads"], "tile": oinfo["tile"],
+            "status": int(ost)}
     finally:
         pkg.lbm_batch_destroy(b)
         for s in solvers:

@@ -65,7 +65,10 @@ static void bulk_st(const Params& p, int rows, bool pairs, dim3 g, dim3 b, cudaS
   // covers pairs of cells along x)
   const int rs = rows & ROWS_MASK;
   const bool fast = rs == ROWS_INNER || (rs == ROWS_ALL && p.px && p.py);
-  if (fast && pairs) launch_prio(k_bulk2<LBM_Q, ST>, g, b, s, prio, p, rows);
+  if (fast && pairs) {
+    if (p.collision == 0) launch_prio(k_bulk2<LBM_Q, ST, COLL_BGK>, g, b, s, prio, p, rows);
+    else launch_prio(k_bulk2<LBM_Q, ST, COLL_REG>, g, b, s, prio, p, rows);
+  }
   else if (fast) launch_prio(k_bulk<LBM_Q, ST, false>, g, b, s, prio, p, rows);
   else launch_prio(k_bulk<LBM_Q, ST, true>, g, b, s, prio, p, rows);
 }

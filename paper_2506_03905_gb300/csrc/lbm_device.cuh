@@ -43,6 +43,8 @@ enum BcKind {
 };
 enum { XMIN = 0, XMAX = 1, YMIN = 2, YMAX = 3 };
 enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2, ST_FP64 = 3 };
+// collision operator of a kernel instantiation (Params::collision: 0 BGK, 1 regularized)
+enum { COLL_ANY = -1, COLL_BGK = 0, COLL_REG = 1 };
 // flags[0]: failure bits; flags[1]: wall-node updates whose Newton iteration
 // reached its limit (count); flags[2..3] unused
 enum { FLAG_NONFINITE = 1u, FLAG_NEWTON = 2u, FLAG_TMA_TIMEOUT = 4u };
@@ -136,6 +138,14 @@ template <> struct Codec<ST_FP32> {
   __device__ static __forceinline__ void st2_raw(T* p, float a, float b) {
     *reinterpret_cast<float2*>(p) = make_float2(a, b);
   }
+  // a pair of raw values as loaded (P2), read from p[0], p[1] in one access or
+  // from two addresses, and its two values in the compute type
+  using P2 = float2;
+  __device__ static __forceinline__ P2 ld_pair(const T* p) { return *reinterpret_cast<const float2*>(p); }
+  __device__ static __forceinline__ P2 pair(const T* a, const T* b) { return make_float2(*a, *b); }
+  __device__ static __forceinline__ float lo(P2 v) { return v.x; }
+  __device__ static __forceinline__ float hi(P2 v) { return v.y; }
+  __device__ static __forceinline__ float2 both(P2 v) { return v; }
 };
 template <> struct Codec<ST_FP64> {
   using T = double;
@@ -152,6 +162,11 @@ template <> struct Codec<ST_FP64> {
   __device__ static __forceinline__ void st2_raw(T* p, double a, double b) {
     *reinterpret_cast<double2*>(p) = make_double2(a, b);
   }
+  using P2 = double2;
+  __device__ static __forceinline__ P2 ld_pair(const T* p) { return *reinterpret_cast<const double2*>(p); }
+  __device__ static __forceinline__ P2 pair(const T* a, const T* b) { return make_double2(*a, *b); }
+  __device__ static __forceinline__ double lo(P2 v) { return v.x; }
+  __device__ static __forceinline__ double hi(P2 v) { return v.y; }
 };
 template <> struct Codec<ST_FP16> {
   using T = __half;
@@ -168,6 +183,13 @@ template <> struct Codec<ST_FP16> {
   __device__ static __forceinline__ void st2_raw(T* p, float a, float b) {
     *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);   // one packed conversion
   }
+  // a pair stays in one 32-bit register until it is converted
+  using P2 = __half2;
+  __device__ static __forceinline__ P2 ld_pair(const T* p) { return *reinterpret_cast<const __half2*>(p); }
+  __device__ static __forceinline__ P2 pair(const T* a, const T* b) { return __halves2half2(*a, *b); }
+  __device__ static __forceinline__ float lo(P2 v) { return __low2float(v); }
+  __device__ static __forceinline__ float hi(P2 v) { return __high2float(v); }
+  __device__ static __forceinline__ float2 both(P2 v) { return __half22float2(v); }
 };
 template <> struct Codec<ST_BF16> {
   using T = __nv_bfloat16;
@@ -184,6 +206,14 @@ template <> struct Codec<ST_BF16> {
   __device__ static __forceinline__ void st2_raw(T* p, float a, float b) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
   }
+  using P2 = __nv_bfloat162;
+  __device__ static __forceinline__ P2 ld_pair(const T* p) {
+    return *reinterpret_cast<const __nv_bfloat162*>(p);
+  }
+  __device__ static __forceinline__ P2 pair(const T* a, const T* b) { return __halves2bfloat162(*a, *b); }
+  __device__ static __forceinline__ float lo(P2 v) { return __low2float(v); }
+  __device__ static __forceinline__ float hi(P2 v) { return __high2float(v); }
+  __device__ static __forceinline__ float2 both(P2 v) { return __bfloat1622float2(v); }
 };
 template <int ST> struct Compute { using R = float; };
 template <> struct Compute<ST_FP64> { using R = double; };
@@ -891,7 +921,10 @@ __device__ __forceinline__ void eq_pair(const EqCoef<R>& k, int cx, R d, R* ev, 
   }
 }
 
-template <int Q, class R, int SCALE = 1>
+// COLL: the collision operator fixed at compile time (COLL_BGK, COLL_REG), or
+// COLL_ANY to take p.collision at run time; a kernel compiled for one operator
+// needs only that operator's registers.
+template <int Q, class R, int SCALE = 1, int COLL = COLL_ANY>
 __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* u_out) {
   using L = Lat<Q>;
   // moments over opposite pairs (i, i+1 = opp i): the pair's sum enters rho,
@@ -935,7 +968,7 @@ __device__ __forceinline__ void collide(const Params& p, R (&g)[Q], R delta, R* 
   const R fpre = ((R)0.5 * (R)SCALE) * delta;
   const R uF3 = (R)3 * (ux * Fx + uy * Fy + uz * Fz);
   const R fw1 = fpre * (R)L::w(1) * uF3, fw2 = fpre * (R)L::w(Q == 19 ? 7 : 5) * uF3;
-  if (p.collision == 0) {
+  if (COLL == COLL_BGK || (COLL == COLL_ANY && p.collision == 0)) {
     // BGK over opposite pairs: h* = (2 h^eq - h) + delta (h - h^eq) + forcing,
     // the force term of the pair split into its even part fe and odd part fo,
     //   F_{i / opp} = fe +/- fo,  fe = fpre (3 s A_i - 3 w u.F),  fo = fpre A_i

@@ -123,7 +123,7 @@ __device__ __forceinline__ void bulk_interior(const Params& p, int x, int y, int
 // shared, and the FP32 arithmetic runs on packed lanes (f2).  Each cell follows
 // the steps of bulk_interior; the packed lanes round products and sums
 // separately where the scalar code may fuse them.
-template <int Q, int ST>
+template <int Q, int ST, int COLL>
 __device__ __forceinline__ void bulk_interior2(const Params& p, int x0, int y, int z) {
   using L = Lat<Q>;
   using C = Codec<ST>;
@@ -142,25 +142,18 @@ __device__ __forceinline__ void bulk_interior2(const Params& p, int x0, int y, i
   R* LBM_RESTRICT vd = (R*)p.v_dst;
   const NbOff o = nb_offsets(p, x0, y, z);     // cell A; B has x - 1 = A
   const int oxpB = x0 + 1 == p.nx - 1 ? -(p.nx - 1) : 1;
-  // pull streaming (Eq. 3) for both cells, issued first
-  R gA[Q], gB[Q];
+  // pull streaming (Eq. 3) for both cells, issued first; the pairs are kept as
+  // loaded (16-bit storage: one 32-bit register per direction) through the SA
+  // stencil and converted just before the collision
+  typename C::P2 hp[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
     const int yz = (cy > 0 ? o.oym : (cy < 0 ? o.oyp : 0)) + (cz > 0 ? o.ozm : (cz < 0 ? o.ozp : 0));
     const T* pa = fs + (i * o.nc + o.id + yz);   // element x0 of the source row
-    if (cx == 0) {
-      R a, b;
-      C::ld2_raw(pa, &a, &b);
-      gA[i] = a;
-      gB[i] = b;
-    } else if (cx > 0) {                          // sources x0 - 1 (wrapped) and x0
-      gA[i] = (R)C::ld_raw(pa + o.oxm);
-      gB[i] = (R)C::ld_raw(pa);
-    } else {                                      // sources x0 + 1 and x0 + 2 (wrapped)
-      gA[i] = (R)C::ld_raw(pa + 1);
-      gB[i] = (R)C::ld_raw(pa + 1 + oxpB);
-    }
+    if (cx == 0) hp[i] = C::ld_pair(pa);
+    else if (cx > 0) hp[i] = C::pair(pa + o.oxm, pa);      // sources x0 - 1 (wrapped) and x0
+    else hp[i] = C::pair(pa + 1, pa + 1 + oxpB);           // sources x0 + 1 and x0 + 2 (wrapped)
   }
   // SA working variable of the new step (Eq. 11): the records of both stencils
   R ntA, ntB;
@@ -199,11 +192,11 @@ __device__ __forceinline__ void bulk_interior2(const Params& p, int x0, int y, i
   if constexpr (kPacked) {
     f2 g[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = f2(gA[i], gB[i]);
+    for (int i = 0; i < Q; ++i) g[i] = f2(C::both(hp[i]));
     const f2 nt(ntA, ntB), nu = psel<f2>(p.nu, p.nu_f), inu = psel<f2>(p.inv_nu, p.inv_nu_f);
     const f2 nut = p.turbulent ? sa_nut<f2>(nt, inu) : f2(0.0f);
     f2 u[3];
-    collide<Q, f2, C::kScale>(p, g, relax_delta<f2>(f2(3.0f) * (nu + nut)), u);   // 2 - omega (Eq. 8)
+    collide<Q, f2, C::kScale, COLL>(p, g, relax_delta<f2>(f2(3.0f) * (nu + nut)), u);   // 2 - omega (Eq. 8)
 #pragma unroll
     for (int i = 0; i < Q; ++i) C::st2_raw(fd + (i * o.nc + o.id), g[i].v.x, g[i].v.y);
     st_rec(vd, o.id, u[0].v.x, u[1].v.x, u[2].v.x, ntA);
@@ -212,9 +205,15 @@ __device__ __forceinline__ void bulk_interior2(const Params& p, int x0, int y, i
     const R nu = psel<R>(p.nu, p.nu_f), inu = psel<R>(p.inv_nu, p.inv_nu_f);
     const R nutA = p.turbulent ? sa_nut<R>(ntA, inu) : (R)0;
     const R nutB = p.turbulent ? sa_nut<R>(ntB, inu) : (R)0;
+    R gA[Q], gB[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      gA[i] = C::lo(hp[i]);
+      gB[i] = C::hi(hp[i]);
+    }
     R uA[3], uB[3];
-    collide<Q, R, C::kScale>(p, gA, relax_delta<R>((R)3 * (nu + nutA)), uA);   // 2 - omega (Eq. 8)
-    collide<Q, R, C::kScale>(p, gB, relax_delta<R>((R)3 * (nu + nutB)), uB);
+    collide<Q, R, C::kScale, COLL>(p, gA, relax_delta<R>((R)3 * (nu + nutA)), uA);   // 2 - omega (Eq. 8)
+    collide<Q, R, C::kScale, COLL>(p, gB, relax_delta<R>((R)3 * (nu + nutB)), uB);
 #pragma unroll
     for (int i = 0; i < Q; ++i) C::st2_raw(fd + (i * o.nc + o.id), gA[i], gB[i]);
     st_rec(vd, o.id, uA[0], uA[1], uA[2], ntA);
@@ -402,12 +401,23 @@ __device__ __forceinline__ void bulk_cell(const Params& p, int x, int y, int z) 
 // inside the lattice take bulk_interior2, the lone cell of a row end (odd nx,
 // or a pair cut by the x-face columns of a non-periodic x axis) bulk_interior.
 // Registers: two cells' populations are live at once; the budget is set by
-// LBM_BULK2_MINB blocks of LBM_BULK_THREADS per SM.
+// LBM_BULK2_MINB blocks of LBM_BULK_THREADS per SM (LBM_BULK2_MINB16 for
+// 16-bit storage).  One instantiation per collision operator (COLL): with the
+// operator chosen at run time the regularized operator's moments set the
+// register peak of BGK lattices too (BGK channel 256x128x128, 1000 steps: FP16
+// 36.5k -> 39.2k MLUPS, BF16 36.4k -> 37.1k, FP32 unchanged at 34.8k).  A
+// budget of 80 registers for 16-bit storage (12 blocks of 64 threads per SM)
+// gave 39.4k / 37.3k against 96 registers' 39.2k / 37.1k.
 #ifndef LBM_BULK2_MINB
 #define LBM_BULK2_MINB 10
 #endif
-template <int Q, int ST>
-__global__ void __launch_bounds__(LBM_BULK_THREADS, LBM_BULK2_MINB) k_bulk2(const Params p, int rows_arg) {
+#ifndef LBM_BULK2_MINB16
+#define LBM_BULK2_MINB16 12
+#endif
+template <int Q, int ST, int COLL>
+__global__ void __launch_bounds__(LBM_BULK_THREADS, (ST == ST_FP16 || ST == ST_BF16) ? LBM_BULK2_MINB16
+                                                                                      : LBM_BULK2_MINB)
+    k_bulk2(const Params p, int rows_arg) {
   const bool zy = rows_arg & ROWS_ZY;
   const int rows = rows_arg & ROWS_MASK;
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -418,7 +428,7 @@ __global__ void __launch_bounds__(LBM_BULK_THREADS, LBM_BULK2_MINB) k_bulk2(cons
   // x-face columns of a non-periodic x axis belong to the ROWS_XEDGE launch
   const bool inA = p.px || (x0 >= 1 && x0 <= p.nx - 2);
   const bool inB = x0 + 1 < p.nx && (p.px || x0 + 1 <= p.nx - 2);
-  if (inA && inB) bulk_interior2<Q, ST>(p, x0, y, z);
+  if (inA && inB) bulk_interior2<Q, ST, COLL>(p, x0, y, z);
   else if (inA) bulk_interior<Q, ST>(p, x0, y, z);
   else if (inB) bulk_interior<Q, ST>(p, x0 + 1, y, z);
 }
