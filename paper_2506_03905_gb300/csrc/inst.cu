@@ -74,7 +74,8 @@ static void bulk_st(const Params& p, int rows, bool pairs, dim3 g, dim3 b, cudaS
 }
 template <int ST>
 static void wall_st(const Params& p, bool regularized, dim3 g, dim3 b, cudaStream_t s, int prio) {
-  if (regularized) launch_prio(k_wall<LBM_Q, ST, WALLS_REG>, g, b, s, prio, p);
+  if (regularized && p.collision == 0) launch_prio(k_wall<LBM_Q, ST, WALLS_REG, COLL_BGK>, g, b, s, prio, p);
+  else if (regularized) launch_prio(k_wall<LBM_Q, ST, WALLS_REG, COLL_REG>, g, b, s, prio, p);
   else launch_prio(k_wall<LBM_Q, ST, WALLS_BB>, g, b, s, prio, p);
 }
 

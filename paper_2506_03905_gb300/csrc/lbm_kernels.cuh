@@ -606,8 +606,10 @@ __global__ void __launch_bounds__(256, LBM_TMA_MINB)
 // WALLS: the wall class the caller has checked (WALLS_BB: slip bounce-back,
 // WALLS_REG: regularized, HRFD or Cai-Degrigny), whose branch alone is compiled;
 // WALLS_ANY decides per face at run time.
+// COLL: the collision operator of a regularized node's own step (COLL_ANY:
+// p.collision at run time).
 enum { WALLS_ANY = 0, WALLS_BB = 1, WALLS_REG = 2 };
-template <int Q, int ST, int WALLS = WALLS_ANY>
+template <int Q, int ST, int WALLS = WALLS_ANY, int COLL = COLL_ANY>
 __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
   using L = Lat<Q>;
   using C = Codec<ST>;
@@ -789,7 +791,7 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
     const R ntn = p.turbulent ? psel<R>(p.nu, p.nu_f) * (R)WF::kappa * ypB : ntB;
     const R nutn = p.turbulent ? sa_nut<R>(ntn, psel<R>(p.inv_nu, p.inv_nu_f)) : (R)0;
     R u[3];
-    collide<Q, R>(p, g, relax_delta<R>((R)3 * (psel<R>(p.nu, p.nu_f) + nutn)), u);   // Eq. 8
+    collide<Q, R, 1, COLL>(p, g, relax_delta<R>((R)3 * (psel<R>(p.nu, p.nu_f) + nutn)), u);   // Eq. 8
     T* LBM_RESTRICT fdst = (T*)p.f_dst;
 #pragma unroll
     for (int i = 0; i < Q; ++i) C::st(fdst + i * p.ncell + idB, g[i]);
@@ -816,15 +818,18 @@ __device__ __forceinline__ void wall_node(const Params& p, int fi, int node) {
 #define LBM_WALL_REG_MINB LBM_WALL_MINB   // the regularized class's budget
 #endif
 // One kernel per wall class (WALLS_BB / WALLS_REG), so that a warp's code holds
-// one scheme only; a face of the other class is left to the other kernel.
-template <int Q, int ST, int WALLS>
+// one scheme only; a face of the other class is left to the other kernel.  The
+// regularized class is compiled once per collision operator of the nodes' own
+// step (FP32, 64 registers: 44 B of spill stores per thread with the operator
+// chosen at run time, 4 B for BGK only).
+template <int Q, int ST, int WALLS, int COLL = COLL_ANY>
 __global__ void __launch_bounds__(128, WALLS == WALLS_BB ? LBM_WALL_MINB : LBM_WALL_REG_MINB)
     k_wall(const Params p) {
   const int fi = blockIdx.y;
   if (!p.wall[fi] || (p.wall[fi] == BC_WALL_BB) != (WALLS == WALLS_BB)) return;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < p.nwall[fi];
        node += gridDim.x * blockDim.x)
-    wall_node<Q, ST, WALLS>(p, fi, node);
+    wall_node<Q, ST, WALLS, COLL>(p, fi, node);
 }
 
 // ----------------------------------------------------------------------------
