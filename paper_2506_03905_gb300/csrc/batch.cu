@@ -91,6 +91,7 @@ struct BatchCtl {
   unsigned pad;
 };
 
+constexpr int kCtlSlots = 4;    // control copies of launches in flight
 constexpr long long kSpinLimit = 1LL << 24;   // x ~64 ns sleep: about one second
 
 // Lane 0 waits until *ctr >= target; false if the wait gave up or another warp
@@ -280,7 +281,6 @@ BatchKernel batch_kernel(int st, int q) { return q == 19 ? batch_kernel_q<19>(st
 #define LBM_MULTI_CELLS 128
 #endif
 constexpr int kMultiCells = LBM_MULTI_CELLS;   // cells per B / I / W item, one per thread
-constexpr int kMultiCellsMinB = 16384 / LBM_MULTI_CELLS;   // 64 registers
 constexpr int kMultiNodes = 128;   // wall nodes per A item, one per thread
 enum { MK_A = 0, MK_I = 1, MK_BW = 2 };
 
@@ -305,16 +305,32 @@ __global__ void __launch_bounds__(kMultiNodes, 8) k_multi_a(const BatchInst* ins
 }
 
 template <int ST, int Q, bool FACE_FREE>
-__global__ void __launch_bounds__(kMultiCells, kMultiCellsMinB) k_multi_cells(const BatchInst* inst,
-                                                                const WorkItem* items, int step) {
-  __shared__ Params sp;
+__device__ __forceinline__ void multi_cells(Params* sp, const BatchInst* inst, const WorkItem* items,
+                                            int step) {
   const WorkItem w = items[blockIdx.x];
-  const Params& p = cta_params(&sp, inst[w.inst], step);
+  const Params& p = cta_params(sp, inst[w.inst], step);
   const int c = w.begin + threadIdx.x;
   if (c >= w.end) return;
   const BoxWalk at(w, c);
   if (FACE_FREE) bulk_interior<Q, ST>(p, at.x(w), at.y(w), at.z);
   else bulk_cell<Q, ST, true>(p, at.x(w), at.y(w), at.z);
+}
+
+// The cell kernels at the compiler's register choice (FP32, FP64: 72-92
+// registers for D3Q19) and, for 16-bit storage, at 64 registers (8 blocks per
+// SM): on the 96-instance sweep FP16 27.1k -> 28.4k MLUPS, while 64 registers
+// made FP32 slower (27.1k -> 26.5k).
+template <int ST, int Q, bool FACE_FREE>
+__global__ void __launch_bounds__(kMultiCells) k_multi_cells(const BatchInst* inst,
+                                                             const WorkItem* items, int step) {
+  __shared__ Params sp;
+  multi_cells<ST, Q, FACE_FREE>(&sp, inst, items, step);
+}
+template <int ST, int Q, bool FACE_FREE>
+__global__ void __launch_bounds__(kMultiCells, 1024 / kMultiCells)
+    k_multi_cells64(const BatchInst* inst, const WorkItem* items, int step) {
+  __shared__ Params sp;
+  multi_cells<ST, Q, FACE_FREE>(&sp, inst, items, step);
 }
 
 // Buffer parities of every instance advanced by the steps of a launch sequence.
@@ -325,7 +341,11 @@ __global__ void k_multi_advance(BatchInst* inst, int n, int nsteps) {
 
 using MultiKernel = void (*)(const BatchInst*, const WorkItem*, int);
 template <int Q, int ST> MultiKernel multi_kernel_st(int kind) {
-  return kind == MK_A ? k_multi_a<ST, Q> : (kind == MK_I ? k_multi_cells<ST, Q, true> : k_multi_cells<ST, Q, false>);
+  if (kind == MK_A) return k_multi_a<ST, Q>;
+  if constexpr (ST == ST_FP16 || ST == ST_BF16)
+    return kind == MK_I ? k_multi_cells64<ST, Q, true> : k_multi_cells64<ST, Q, false>;
+  else
+    return kind == MK_I ? k_multi_cells<ST, Q, true> : k_multi_cells<ST, Q, false>;
 }
 template <int Q> MultiKernel multi_kernel_q(int st, int kind) {
   switch (st) {
@@ -365,9 +385,14 @@ struct lbm_batch {
   int g_nsteps = -1;
   std::vector<int> dev_cur;      // buffer parity of each instance as the device holds it
   long long spin_limit = kSpinLimit;   // polls before a warp gives up at a wait
-  BatchCtl* h_ctl = nullptr;     // pinned copy of the groups' control blocks after each launch
-  cudaEvent_t ev_ctl = nullptr;
-  bool ctl_pending = false;      // a launch's control copy has not been inspected yet
+  // pinned copies of the groups' control blocks, one pair per launch in flight
+  // (a ring of kCtlSlots): a later launch cannot overwrite the copy of an
+  // earlier one before the host has read it
+  BatchCtl* h_ctl = nullptr;
+  cudaEvent_t ev_ctl[kCtlSlots] = {};
+  bool ctl_pending[kCtlSlots] = {};   // the slot's copy has not been inspected yet
+  int ctl_next = 0;                   // slot of the next launch's copy (the oldest one)
+  bool ctl_failed = false;            // an inspected copy showed a wait that gave up
   // mode 1 (multi-instance launches): items per group and kind (MK_A, MK_I, MK_BW)
   int mode = 0;                  // 0: persistent ticketed kernel, 1: multi-instance launches
   int forced_mode = -1;          // lbm_batch_set_mode; -1: the autotuner's choice
@@ -598,11 +623,26 @@ static lbm_status launch(lbm_batch* b, int nsteps, cudaStream_t s) {
 
 // After a launch on b->stream: copy the control block to pinned host memory
 // behind it, to be inspected later without blocking the host.
+static void inspect_ctl(lbm_batch* b, int slot) {
+  BatchCtl* h = b->h_ctl + 2 * slot;
+  b->ctl_pending[slot] = false;
+  if (h[0].err || h[1].err) b->ctl_failed = true;
+  h[0].err = h[1].err = 0;
+}
+
 static lbm_status queue_ctl_copy(lbm_batch* b) {
-  BATCH_TRY(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, 2 * sizeof(BatchCtl), cudaMemcpyDeviceToHost,
-                               b->stream));
-  BATCH_TRY(b, cudaEventRecord(b->ev_ctl, b->stream));
-  b->ctl_pending = true;
+  const int slot = b->ctl_next;
+  if (b->ctl_pending[slot]) {
+    // kCtlSlots launches in flight: the oldest one's copy is read before its
+    // slot is reused (this call then waits for that launch)
+    BATCH_TRY(b, cudaEventSynchronize(b->ev_ctl[slot]));
+    inspect_ctl(b, slot);
+  }
+  BATCH_TRY(b, cudaMemcpyAsync(b->h_ctl + 2 * slot, b->d_ctl, 2 * sizeof(BatchCtl),
+                               cudaMemcpyDeviceToHost, b->stream));
+  BATCH_TRY(b, cudaEventRecord(b->ev_ctl[slot], b->stream));
+  b->ctl_pending[slot] = true;
+  b->ctl_next = (slot + 1) % kCtlSlots;
   return LBM_OK;
 }
 
@@ -611,17 +651,22 @@ static lbm_status queue_ctl_copy(lbm_batch* b) {
 // a reported timeout the instances' states are not valid; the device parities
 // are re-sent before the next launch.
 static lbm_status poll_ctl(lbm_batch* b, bool blocking) {
-  if (!b->ctl_pending) return LBM_OK;
-  if (blocking) {
-    BATCH_TRY(b, cudaEventSynchronize(b->ev_ctl));
-  } else {
-    const cudaError_t q = cudaEventQuery(b->ev_ctl);
-    if (q == cudaErrorNotReady) return LBM_OK;
-    BATCH_TRY(b, q);
+  // the slots in launch order, oldest first (all copies are on b->stream, so a
+  // copy is complete only if every older one is)
+  for (int k = 0; k < kCtlSlots; ++k) {
+    const int slot = (b->ctl_next + k) % kCtlSlots;
+    if (!b->ctl_pending[slot]) continue;
+    if (blocking) {
+      BATCH_TRY(b, cudaEventSynchronize(b->ev_ctl[slot]));
+    } else {
+      const cudaError_t q = cudaEventQuery(b->ev_ctl[slot]);
+      if (q == cudaErrorNotReady) break;
+      BATCH_TRY(b, q);
+    }
+    inspect_ctl(b, slot);
   }
-  b->ctl_pending = false;
-  if (b->h_ctl[0].err || b->h_ctl[1].err) {
-    b->h_ctl[0].err = b->h_ctl[1].err = 0;
+  if (b->ctl_failed) {
+    b->ctl_failed = false;
     for (int& d : b->dev_cur) d = -1;
     b->err = "a bounded wait of the batch kernel gave up; the instances' states are not valid";
     return LBM_ETIMEOUT;
@@ -714,8 +759,7 @@ extern "C" lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** 
   }
   if (cudaMalloc(&b->d_inst, n * sizeof(BatchInst)) != cudaSuccess ||
       cudaMalloc(&b->d_ctl, b->ctl_bytes) != cudaSuccess ||
-      cudaMallocHost(&b->h_ctl, 2 * sizeof(BatchCtl)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_ctl, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&b->h_ctl, 2 * kCtlSlots * sizeof(BatchCtl)) != cudaSuccess ||
       cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, b->prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
@@ -723,7 +767,15 @@ extern "C" lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** 
     lbm_batch_destroy(b);
     return LBM_ENOMEM;
   }
-  std::memset(b->h_ctl, 0, 2 * sizeof(BatchCtl));
+  for (cudaEvent_t& e : b->ev_ctl) {
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      e = nullptr;
+      g_batch_err = "lbm_batch_create: event creation failed";
+      lbm_batch_destroy(b);
+      return LBM_ENOMEM;
+    }
+  }
+  std::memset(b->h_ctl, 0, 2 * kCtlSlots * sizeof(BatchCtl));
   // the contexts' pending work (state set-up) must be complete before the batch
   // reads their parameters on another order of launches
   for (lbm_ctx* c : b->ctxs) cudaStreamSynchronize(c->stream);
@@ -906,7 +958,8 @@ extern "C" void lbm_batch_destroy(lbm_batch* b) {
   if (b->d_ctl) cudaFree(b->d_ctl);
   if (b->d_items) cudaFree(b->d_items);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
-  if (b->ev_ctl) cudaEventDestroy(b->ev_ctl);
+  for (cudaEvent_t& e : b->ev_ctl)
+    if (e) cudaEventDestroy(e);
   if (b->d_mitems) cudaFree(b->d_mitems);
   if (b->side) {
     cudaStreamSynchronize(b->side);

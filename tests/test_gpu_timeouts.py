@@ -8,6 +8,9 @@ LBM_ETIMEOUT.  A test-only limit of 0 polls makes the waits give up at once:
   every warp leaves at its next ticket or wait, lbm_batch_wait reports
   LBM_ETIMEOUT; with the default limit restored and the states set again the
   same batch then computes what single instances compute;
+* a launch that gave up is reported even when the host enqueues another,
+  successful launch before it looks (each launch's failure record has its own
+  host copy);
 * the TMA-staged inner-row kernel: every block gives up on its first tile,
   waits (with the default bound) for its copies in flight and leaves;
   lbm_fields reports LBM_ETIMEOUT, and the context is usable again after a
@@ -62,6 +65,32 @@ def test_batch_wait_runs_out_and_the_batch_recovers():
         s.close()
     for c, g, r in zip(cases, got, ref):
         assert rel(g, r) < 1e-6, c.name
+
+
+def test_batch_timeout_is_reported_after_a_later_launch():
+    import paper_2506_03905_gb300 as pkg
+    from test_gpu_batch import mixed_cases, solvers
+    cases = mixed_cases()
+    ss = solvers(cases)
+    b = pkg.lbm_batch_create([s.ctx for s in ss])
+    pkg.lbm_batch_set_mode(b, 0)
+    pkg.lbm_batch_tune(b)
+    assert pkg.lbm_batch_wait(b) == pkg.LBM_OK
+    pkg.lbm_batch_set_wait_limit(b, 0)
+    pkg.lbm_batch_step(b, 3)          # gives up
+    pkg.lbm_batch_set_wait_limit(b, DEFAULT_POLLS)
+    # enqueued before the host has looked at the first launch, if that one is
+    # still running; otherwise this call already reports it
+    try:
+        pkg.lbm_batch_step(b, 3)
+        st = pkg.lbm_batch_wait(b)
+    except pkg.LbmError as exc:
+        st = exc.status
+    assert st == pkg.LBM_ETIMEOUT
+    assert pkg.lbm_batch_wait(b) == pkg.LBM_OK
+    pkg.lbm_batch_destroy(b)
+    for s in ss:
+        s.close()
 
 
 def test_tma_tile_wait_runs_out_and_the_context_recovers():
