@@ -337,7 +337,10 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** out);
    call unless lbm_batch_tune fixed them; the autotuner advances every instance
    while it times (28 steps).  A bounded wait of an earlier launch that gave up
    is reported here (LBM_ETIMEOUT) once that launch has finished, or by
-   lbm_batch_wait; the instances' states are then not valid. */
+   lbm_batch_wait, also when later launches were enqueued meanwhile; the
+   instances' states are then not valid.  Each launch's failure record is copied
+   to its own host slot; with four launches of the persistent kernel still in
+   flight, the next call first waits for the oldest. */
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
 /* Time the candidate tile sizes (64, 256, 1024 cells per warp item) and block
    sizes (128, 256 threads) of mode 0 and the launches of mode 1 once, keep the
