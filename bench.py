@@ -124,7 +124,8 @@ class ClockSampler:
 
     def _wait_lines(self, n: int, limit_s: float):
         t0 = time.perf_counter()
-        while self.proc is not None and self._lines() < n and time.perf_counter() - t0 < limit_s:
+        while (self.proc is not None and self.proc.poll() is None and self._lines() < n
+               and time.perf_counter() - t0 < limit_s):
             time.sleep(0.005)
 
     def stop(self):
